@@ -1,0 +1,279 @@
+// Fused energy epilogue (S4) and deterministic reductions (S5).
+//
+// For a task (i,j,k) with i <= j <= k the energy share is
+//   e_ijk = (m/6) sum_{abc} Z^{abc} (W^{abc} + Y^{abc}) / D^{abc},
+//   Z = 8 W^{abc} - 4 (W^{acb} + W^{bac} + W^{cba}) + 2 (W^{bca} + W^{cab}),
+// m the number of distinct orderings of (i,j,k).  This is the sum over those
+// orderings of sum_abc W~ V / D (Eqs. piecuch_4th_order/5th_order with the
+// tilde of Eq. piecuch_tilde_quantity): W, Y and D are invariant under the
+// simultaneous permutations of Eq. (symm_operator), so the orderings of ijk
+// become permutations of abc, and the tilde coefficients (4/3, -2, 2/3)
+// summed over the six orderings give (8, -4 per transposition, 2 per
+// 3-cycle).  E[4] uses W in place of V.
+//
+// One CTA takes one block orbit {A <= B <= C} (blocks of TE virtual indices)
+// of one task: it assembles the W cubes of all six block permutations in
+// shared memory from the three group tensors,
+//   W[x][y][z] = U0[x][y][z] + U1[y][x][z] + U2[z][x][y],
+// reading each U row contiguously, then evaluates Z, Y, D and the two energy
+// sums for every element of the distinct cubes, and reduces them with warp
+// shuffles to one FP64 pair.  Every element (a,b,c) of the task lies in
+// exactly one distinct cube of exactly one orbit.
+#include "tcorr_internal.cuh"
+
+namespace tcorr {
+namespace {
+
+constexpr int NT = 256;
+
+__device__ __forceinline__ void kahan_add(double &s, double &c, double x) {
+    const double y = x - c;
+    const double t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+struct EpiParams {
+    Dims dm;
+    const int *tasks;
+    int64_t task0;
+    const void *U;
+    const double *eps_o, *eps_v;
+    const void *t1, *ovov;
+    const float *dev_f;
+    const int *orbits;
+    int norb;
+    double *partials;
+};
+
+// UT: storage type of U; CT: element arithmetic (double for the FP64
+// precision, float for the mixed precisions); TE: cube edge.
+template <typename UT, typename CT, int TE>
+__global__ void __launch_bounds__(NT) epilogue_kernel(const EpiParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CT *Ws = reinterpret_cast<CT *>(smem_raw);
+    constexpr int TP = TE + 1;               // padded innermost extent
+    constexpr int CUBE = TE * TE * TP;       // smem elements per cube
+    constexpr int NE = TE * TE * TE;         // elements per cube
+    __shared__ int comp[6][6];
+    __shared__ int blk[6][3];
+    __shared__ int distinct[6];
+    __shared__ double red[NT / 32][2];
+
+    const int o = p.dm.o, v = p.dm.v, vc = p.dm.vc;
+    const int64_t v2 = (int64_t)v * v;
+    const int orb = blockIdx.x, tb = blockIdx.y;
+    const int *tk = p.tasks + 3 * (p.task0 + tb);
+    const int ti = tk[0], tj = tk[1], tkk = tk[2];
+    double *out = p.partials + ((int64_t)tb * p.norb + orb) * 2;
+    if (ti == tj && tj == tkk) {  // Z = 0 identically
+        if (threadIdx.x == 0) { out[0] = 0.0; out[1] = 0.0; }
+        return;
+    }
+    const int tid = threadIdx.x;
+    const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    if (tid < 36) {
+        const int pi = tid / 6, q = tid % 6;
+        const int t0 = P[pi][P[q][0]], t1 = P[pi][P[q][1]], t2 = P[pi][P[q][2]];
+        int sig = 0;
+        for (int s = 0; s < 6; s++)
+            if (P[s][0] == t0 && P[s][1] == t1 && P[s][2] == t2) sig = s;
+        comp[pi][q] = sig;
+    }
+    if (tid < 6) {
+        const int ob[3] = {p.orbits[3 * orb], p.orbits[3 * orb + 1], p.orbits[3 * orb + 2]};
+        blk[tid][0] = ob[P[tid][0]];
+        blk[tid][1] = ob[P[tid][1]];
+        blk[tid][2] = ob[P[tid][2]];
+    }
+    __syncthreads();
+    if (tid < 6) {
+        int d = 1;
+        for (int s = 0; s < tid; s++)
+            if (blk[s][0] == blk[tid][0] && blk[s][1] == blk[tid][1] && blk[s][2] == blk[tid][2]) d = 0;
+        distinct[tid] = d;
+    }
+
+    const UT *U0 = static_cast<const UT *>(p.U) + (int64_t)(tb * 3 + 0) * v2 * vc;
+    const UT *U1 = U0 + v2 * vc;
+    const UT *U2 = U1 + v2 * vc;
+
+    // pass A: W = U0[x][y][z] + U1[y][x][z]   (z fastest: contiguous rows)
+    for (int e = tid; e < 6 * NE; e += NT) {
+        const int s = e / NE, l = e % NE;
+        const int l0 = l / (TE * TE), l1 = (l / TE) % TE, l2 = l % TE;
+        const int x = blk[s][0] * TE + l0, y = blk[s][1] * TE + l1, z = blk[s][2] * TE + l2;
+        CT w = CT(0);
+        if (x < v && y < v && z < v)
+            w = CT(U0[((int64_t)x * v + y) * vc + z]) + CT(U1[((int64_t)y * v + x) * vc + z]);
+        Ws[s * CUBE + (l0 * TE + l1) * TP + l2] = w;
+    }
+    __syncthreads();
+    // pass B: W += U2[z][x][y]   (y fastest: contiguous rows)
+    for (int e = tid; e < 6 * NE; e += NT) {
+        const int s = e / NE, l = e % NE;
+        const int l2 = l / (TE * TE), l0 = (l / TE) % TE, l1 = l % TE;
+        const int x = blk[s][0] * TE + l0, y = blk[s][1] * TE + l1, z = blk[s][2] * TE + l2;
+        if (x < v && y < v && z < v)
+            Ws[s * CUBE + (l0 * TE + l1) * TP + l2] += CT(U2[((int64_t)z * v + x) * vc + y]);
+    }
+    __syncthreads();
+
+    const CT *t1 = static_cast<const CT *>(p.t1);
+    const CT *ov = static_cast<const CT *>(p.ovov);
+    const double eijk = p.eps_o[ti] + p.eps_o[tj] + p.eps_o[tkk];
+    const CT coef[6] = {CT(8), CT(-4), CT(-4), CT(2), CT(2), CT(-4)};
+    // ovov rows used by Y: (j y | k z), (i x | k z), (i x | j y)
+    const CT *ov_jk = ov + ((int64_t)tj * v * o + tkk) * v;   // [y][z] stride o*v in y
+    const CT *ov_ik = ov + ((int64_t)ti * v * o + tkk) * v;   // [x][z]
+    const CT *ov_ij = ov + ((int64_t)ti * v * o + tj) * v;    // [x][y]
+    const int64_t ovs = (int64_t)o * v;
+
+    double s4 = 0.0, c4 = 0.0, s5 = 0.0, c5 = 0.0;
+    for (int s = 0; s < 6; s++) {
+        if (!distinct[s]) continue;
+        CT a4 = CT(0), a5 = CT(0);
+        const int X0 = blk[s][0] * TE, Y0 = blk[s][1] * TE, Z0 = blk[s][2] * TE;
+        CT base = CT(0);
+        if constexpr (sizeof(CT) == 4)
+            base = CT(eijk - p.eps_v[X0 < v ? X0 : 0] - p.eps_v[Y0 < v ? Y0 : 0] -
+                      p.eps_v[Z0 < v ? Z0 : 0]);
+        for (int l = tid; l < NE; l += NT) {
+            const int lv[3] = {l / (TE * TE), (l / TE) % TE, l % TE};
+            const int x = X0 + lv[0], y = Y0 + lv[1], z = Z0 + lv[2];
+            if (x >= v || y >= v || z >= v) continue;
+            CT zv = CT(0);
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+                const int sg = comp[s][q];
+                const int m0 = lv[P[q][0]], m1 = lv[P[q][1]], m2 = lv[P[q][2]];
+                zv += coef[q] * Ws[sg * CUBE + (m0 * TE + m1) * TP + m2];
+            }
+            const CT w0 = Ws[s * CUBE + (lv[0] * TE + lv[1]) * TP + lv[2]];
+            const CT yv = t1[ti * v + x] * ov_jk[y * ovs + z] + t1[tj * v + y] * ov_ik[x * ovs + z] +
+                          t1[tkk * v + z] * ov_ij[x * ovs + y];
+            CT dn;
+            if constexpr (sizeof(CT) == 4)
+                dn = base + (p.dev_f[x] + p.dev_f[y] + p.dev_f[z]);
+            else
+                dn = eijk - p.eps_v[x] - p.eps_v[y] - p.eps_v[z];
+            const CT r = CT(1) / dn;
+            a4 += zv * w0 * r;
+            a5 += zv * yv * r;
+        }
+        kahan_add(s4, c4, double(a4));
+        kahan_add(s5, c5, double(a5));
+    }
+    double r4 = s4 - c4, r5 = s5 - c5;  // fold the compensation
+    for (int off = 16; off > 0; off >>= 1) {
+        r4 += __shfl_xor_sync(0xffffffffu, r4, off);
+        r5 += __shfl_xor_sync(0xffffffffu, r5, off);
+    }
+    if ((tid & 31) == 0) { red[tid >> 5][0] = r4; red[tid >> 5][1] = r5; }
+    __syncthreads();
+    if (tid == 0) {
+        double t4 = 0.0, k4 = 0.0, t5 = 0.0, k5 = 0.0;
+        for (int w = 0; w < NT / 32; w++) { kahan_add(t4, k4, red[w][0]); kahan_add(t5, k5, red[w][1]); }
+        out[0] = t4 - k4;
+        out[1] = t5 - k5;
+    }
+}
+
+// One CTA per task of the batch: Kahan sum of the orbit partials, times m/6.
+__global__ void __launch_bounds__(NT) task_reduce_kernel(const int *tasks, int64_t task0, int norb,
+                                                         const double *partials, double *task_e) {
+    __shared__ double red[NT][2];
+    const int tb = blockIdx.x, tid = threadIdx.x;
+    const double *pp = partials + (int64_t)tb * norb * 2;
+    double s4 = 0.0, c4 = 0.0, s5 = 0.0, c5 = 0.0;
+    for (int n = tid; n < norb; n += NT) { kahan_add(s4, c4, pp[2 * n]); kahan_add(s5, c5, pp[2 * n + 1]); }
+    red[tid][0] = s4 - c4;
+    red[tid][1] = s5 - c5;
+    __syncthreads();
+    for (int w = NT / 2; w > 0; w >>= 1) {
+        if (tid < w) { red[tid][0] += red[tid + w][0]; red[tid][1] += red[tid + w][1]; }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const int *tk = tasks + 3 * (task0 + tb);
+        const int i = tk[0], j = tk[1], k = tk[2];
+        const double m = (i == j && j == k) ? 0.0 : ((i == j || j == k) ? 3.0 : 6.0);
+        task_e[2 * (task0 + tb)] = red[0][0] * (m / 6.0);
+        task_e[2 * (task0 + tb) + 1] = red[0][1] * (m / 6.0);
+    }
+}
+
+// Single CTA: Kahan sum of task energies first..first+count-1 -> (E4, E5, E).
+__global__ void __launch_bounds__(NT) range_sum_kernel(const double *task_e, int64_t first,
+                                                       int64_t count, double *sums) {
+    __shared__ double red[NT][2];
+    const int tid = threadIdx.x;
+    double s4 = 0.0, c4 = 0.0, s5 = 0.0, c5 = 0.0;
+    for (int64_t n = tid; n < count; n += NT) {
+        kahan_add(s4, c4, task_e[2 * (first + n)]);
+        kahan_add(s5, c5, task_e[2 * (first + n) + 1]);
+    }
+    red[tid][0] = s4 - c4;
+    red[tid][1] = s5 - c5;
+    __syncthreads();
+    for (int w = NT / 2; w > 0; w >>= 1) {
+        if (tid < w) { red[tid][0] += red[tid + w][0]; red[tid][1] += red[tid + w][1]; }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        sums[0] = red[0][0];
+        sums[1] = red[0][1];
+        sums[2] = red[0][0] + red[0][1];
+    }
+}
+
+template <typename UT, typename CT, int TE>
+cudaError_t launch_epi_t(const EpiParams &p, int ntb, cudaStream_t st) {
+    const size_t smem = sizeof(CT) * 6 * TE * TE * (TE + 1);
+    auto kern = epilogue_kernel<UT, CT, TE>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)p.norb, (unsigned)ntb);
+    kern<<<grid, NT, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_epilogue(int prec, const EpiArgs &ea, cudaStream_t st) {
+    EpiParams p;
+    p.dm = ea.dm;
+    p.tasks = ea.tasks;
+    p.task0 = ea.task0;
+    p.U = ea.U;
+    p.eps_o = ea.eps_o;
+    p.eps_v = ea.eps_v;
+    p.t1 = ea.t1;
+    p.ovov = ea.ovov;
+    p.dev_f = ea.dev_f;
+    p.orbits = ea.orbits;
+    p.norb = ea.norb;
+    p.partials = ea.partials;
+    if (ea.ntb > 65535) return cudaErrorInvalidConfiguration;
+    if (prec == TCORR_FP64) {
+        if (ea.te != 8) return cudaErrorInvalidValue;
+        return launch_epi_t<double, double, 8>(p, ea.ntb, st);
+    }
+    if (ea.te != 16) return cudaErrorInvalidValue;
+    return launch_epi_t<float, float, 16>(p, ea.ntb, st);
+}
+
+cudaError_t launch_task_reduce(const EpiArgs &ea, cudaStream_t st) {
+    task_reduce_kernel<<<ea.ntb, NT, 0, st>>>(ea.tasks, ea.task0, ea.norb, ea.partials, ea.task_e);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_range_sum(const double *task_e, int64_t first, int64_t count, double *sums,
+                             cudaStream_t st) {
+    range_sum_kernel<<<1, NT, 0, st>>>(task_e, first, count, sums);
+    return cudaGetLastError();
+}
+
+}  // namespace tcorr

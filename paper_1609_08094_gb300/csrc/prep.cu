@@ -1,0 +1,119 @@
+// Layout preparation (S0): re-lays the caller's canonical FP64 blocks into the
+// K-major operand layouts of the W-contraction kernels, zero-padding K, and
+// for the mixed precisions splits each value x into hi = round(x) and
+// lo = round(x - hi) in TF32 or BF16 (the split-precision scheme that replaces
+// the paper's dgemm -> sgemm swap of Sec. 3).
+#include <cuda_bf16.h>
+
+#include "tcorr_internal.cuh"
+
+namespace tcorr {
+namespace {
+
+constexpr int TT = 32;  // transpose tile edge
+
+__device__ __forceinline__ float tf32_rn(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int KIND>
+__device__ __forceinline__ void store_split(void *hi, void *lo, int64_t idx, double x) {
+    if constexpr (KIND == 0) {
+        static_cast<double *>(hi)[idx] = x;
+    } else if constexpr (KIND == 1) {
+        const float h = tf32_rn(static_cast<float>(x));
+        const float l = tf32_rn(static_cast<float>(x - static_cast<double>(h)));
+        static_cast<float *>(hi)[idx] = h;
+        static_cast<float *>(lo)[idx] = l;
+    } else {
+        const __nv_bfloat16 h = __double2bfloat16(x);
+        const __nv_bfloat16 l = __double2bfloat16(x - static_cast<double>(__bfloat162float(h)));
+        static_cast<__nv_bfloat16 *>(hi)[idx] = h;
+        static_cast<__nv_bfloat16 *>(lo)[idx] = l;
+    }
+}
+
+// One CTA (32 x 8 threads) moves a TT x TT tile: rows r (output-contiguous),
+// columns c (input-contiguous when sc = 1).  Tiles are enumerated flat over
+// (b, c-tile, r-tile) in blockIdx.x (64-bit safe through a grid-stride loop).
+template <int KIND>
+__global__ void __launch_bounds__(256) transpose_pad_kernel(
+    const double *__restrict__ in, void *out_hi, void *out_lo, int64_t B, int R, int Rp,
+    int64_t C, int64_t sb, int64_t sr, int64_t sc, int64_t ob, int64_t oc, double scale) {
+    __shared__ double tile[TT][TT + 1];
+    const int64_t nct = (C + TT - 1) / TT;
+    const int64_t nrt = (Rp + TT - 1) / TT;
+    const int64_t ntiles = B * nct * nrt;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t rt = t % nrt;
+        const int64_t ct = (t / nrt) % nct;
+        const int64_t b = t / (nrt * nct);
+        const int64_t r0 = rt * TT, c0 = ct * TT;
+        // load: column c0+tx, rows r0+ty+8m
+        for (int m = 0; m < TT; m += 8) {
+            const int64_t r = r0 + ty + m, c = c0 + tx;
+            double x = 0.0;
+            if (r < R && c < C) x = scale * in[b * sb + r * sr + c * sc];
+            tile[ty + m][tx] = x;
+        }
+        __syncthreads();
+        // store: row c0+ty+8m of the output, element r0+tx
+        for (int m = 0; m < TT; m += 8) {
+            const int64_t c = c0 + ty + m, r = r0 + tx;
+            if (c < C && r < Rp) store_split<KIND>(out_hi, out_lo, b * ob + c * oc + r, tile[tx][ty + m]);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void to_float_kernel(const double *__restrict__ in, float *__restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = static_cast<float>(in[i]);
+}
+
+__global__ void block_deltas_kernel(const double *__restrict__ ev, float *__restrict__ d, int v,
+                                    int te) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < v) d[x] = static_cast<float>(ev[(x / te) * te] - ev[x]);
+}
+
+}  // namespace
+
+cudaError_t launch_transpose_pad(int kind, const double *in, void *out_hi, void *out_lo,
+                                 int64_t B, int R, int Rp, int64_t C, int64_t sb, int64_t sr,
+                                 int64_t sc, int64_t ob, int64_t oc, double scale,
+                                 cudaStream_t st) {
+    const int64_t ntiles = B * ((C + TT - 1) / TT) * ((Rp + TT - 1) / TT);
+    if (ntiles == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)(ntiles < (int64_t)1 << 22 ? ntiles : (int64_t)1 << 22);
+    dim3 blk(TT, 8);
+    if (kind == 0)
+        transpose_pad_kernel<0><<<grid, blk, 0, st>>>(in, out_hi, out_lo, B, R, Rp, C, sb, sr, sc,
+                                                      ob, oc, scale);
+    else if (kind == 1)
+        transpose_pad_kernel<1><<<grid, blk, 0, st>>>(in, out_hi, out_lo, B, R, Rp, C, sb, sr, sc,
+                                                      ob, oc, scale);
+    else
+        transpose_pad_kernel<2><<<grid, blk, 0, st>>>(in, out_hi, out_lo, B, R, Rp, C, sb, sr, sc,
+                                                      ob, oc, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_float(const double *in, float *out, int64_t n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int64_t blocks = (n + 255) / 256;
+    to_float_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_deltas(const double *eps_v, float *dev_f, int v, int te,
+                                cudaStream_t st) {
+    block_deltas_kernel<<<(v + 127) / 128, 128, 0, st>>>(eps_v, dev_f, v, te);
+    return cudaGetLastError();
+}
+
+}  // namespace tcorr

@@ -1,0 +1,214 @@
+"""ctypes binding of libtcorr (include/tcorr.h).
+
+Argument marshalling only: every step of the (T) energy runs in the CUDA
+library.  There is no fallback: if libtcorr.so is missing or cannot be
+loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
+STATUS = ["TCORR_OK", "TCORR_EINVAL", "TCORR_ENOMEM", "TCORR_ECUDA", "TCORR_ETIMEOUT",
+          "TCORR_EUNSUPPORTED"]
+KERNEL_CLASSES = ("prep", "gemm", "epilogue", "reduce")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TcorrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS[status] if 0 <= status < len(STATUS) else f"status {status}"
+        super().__init__(f"{name}: {msg}")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("host_inputs", ctypes.c_int),
+                ("batch_tasks", ctypes.c_int), ("profile", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libtcorr.so (built by __graft_entry__.build() or _build.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libtcorr.so not found at {path}: run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        lib = ctypes.CDLL(path)
+        vp, dp, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+        lib.tcorr_create.restype = ctypes.c_int
+        lib.tcorr_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int,
+                                     vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Opts), vp]
+        lib.tcorr_energy.restype = ctypes.c_int
+        lib.tcorr_energy.argtypes = [vp, dp]
+        lib.tcorr_energy_range.restype = ctypes.c_int
+        lib.tcorr_energy_range.argtypes = [vp, i64, i64, dp, dp]
+        lib.tcorr_num_tasks.restype = i64
+        lib.tcorr_num_tasks.argtypes = [vp]
+        lib.tcorr_task.restype = ctypes.c_int
+        lib.tcorr_task.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int)]
+        lib.tcorr_kernel_times.restype = ctypes.c_int
+        lib.tcorr_kernel_times.argtypes = [vp, dp, ctypes.POINTER(i64), ctypes.c_int]
+        lib.tcorr_device_bytes.restype = i64
+        lib.tcorr_device_bytes.argtypes = [vp]
+        lib.tcorr_destroy.restype = ctypes.c_int
+        lib.tcorr_destroy.argtypes = [vp]
+        lib.tcorr_last_error.restype = ctypes.c_char_p
+        lib.tcorr_last_error.argtypes = [vp]
+        lib.tcorr_status_string.restype = ctypes.c_char_p
+        lib.tcorr_status_string.argtypes = [ctypes.c_int]
+        lib.tcorr_version.restype = ctypes.c_int
+        lib.tcorr_version.argtypes = []
+        _lib = lib
+        return lib
+
+
+EXPORTS = ("tcorr_create", "tcorr_energy", "tcorr_energy_range", "tcorr_num_tasks",
+           "tcorr_task", "tcorr_kernel_times", "tcorr_device_bytes", "tcorr_destroy",
+           "tcorr_last_error", "tcorr_status_string", "tcorr_version")
+
+
+def _shape_check(name, a, shape):
+    if tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(a.shape)}")
+
+
+def _pointer(name, a, on_device: bool):
+    """Raw pointer of a float64 C-contiguous torch tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError(f"{name}: needs a contiguous float64 tensor")
+        if a.is_cuda != on_device:
+            raise ValueError(f"{name}: device/host placement differs from the other inputs")
+        return a.data_ptr()
+    if on_device:
+        raise ValueError(f"{name}: numpy array given together with device tensors")
+    if a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise ValueError(f"{name}: needs a C-contiguous float64 array")
+    return a.ctypes.data
+
+
+class Tcorr:
+    """One (T) problem resident on the GPU.
+
+    Inputs are the seven arrays of tcorr_create (torch CUDA tensors, or all
+    numpy / CPU arrays, which are copied in).  ``prec`` is 'fp64', 'tf32x3' or
+    'bf16x3'.  ``stream``: a torch.cuda.Stream, an integer cudaStream_t, or
+    None for torch's current stream (device inputs) / the default stream."""
+
+    def __init__(self, o, v, eps_occ, eps_vir, t1, t2, vvvo, ooov, ovov, prec="fp64",
+                 batch_tasks=0, profile=False, stream=None):
+        lib = load()
+        arrays = dict(eps_occ=eps_occ, eps_vir=eps_vir, t1=t1, t2=t2, vvvo=vvvo, ooov=ooov,
+                      ovov=ovov)
+        shapes = dict(eps_occ=(o,), eps_vir=(v,), t1=(o, v), t2=(o, o, v, v),
+                      vvvo=(v, v, v, o), ooov=(o, o, o, v), ovov=(o, v, o, v))
+        on_device = bool(getattr(t2, "is_cuda", False))
+        ptrs = []
+        for k, a in arrays.items():
+            _shape_check(k, a, shapes[k])
+            ptrs.append(_pointer(k, a, on_device))
+        if isinstance(prec, str):
+            prec = PREC[prec.lower()]
+        opts = Opts(prec=int(prec), host_inputs=0 if on_device else 1,
+                    batch_tasks=int(batch_tasks), profile=1 if profile else 0)
+        if stream is None and on_device:
+            import torch
+            stream = torch.cuda.current_stream(t2.device)
+        sptr = getattr(stream, "cuda_stream", stream) or 0
+        self._stream = stream
+        self.o, self.v, self.prec = o, v, int(prec)
+        h = ctypes.c_void_p()
+        st = lib.tcorr_create(ctypes.byref(h), int(o), int(v), *ptrs, ctypes.byref(opts),
+                              ctypes.c_void_p(sptr))
+        if st != 0:
+            raise TcorrError(st, lib.tcorr_last_error(None).decode())
+        self._h = h
+
+    @classmethod
+    def from_instance(cls, inst, **kw):
+        return cls(inst.o, inst.v, *inst.arrays(), **kw)
+
+    def _check(self, st):
+        if st != 0:
+            raise TcorrError(st, load().tcorr_last_error(self._h).decode())
+
+    @property
+    def num_tasks(self) -> int:
+        return int(load().tcorr_num_tasks(self._h))
+
+    def task(self, idx: int):
+        ijk = (ctypes.c_int * 3)()
+        self._check(load().tcorr_task(self._h, int(idx), ijk))
+        return tuple(ijk)
+
+    def energy(self):
+        """(E[4], E[5], E(T))."""
+        e = (ctypes.c_double * 3)()
+        self._check(load().tcorr_energy(self._h, e))
+        return tuple(e)
+
+    def energy_range(self, first: int, count: int, per_task: bool = False):
+        """(E[4], E[5], E(T)) of tasks first..first+count-1; with per_task the
+        [count][2] array of (E[4], E[5]) shares is returned as well."""
+        e = (ctypes.c_double * 3)()
+        et = np.zeros((max(count, 0), 2), dtype=np.float64) if per_task else None
+        ptr = et.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if per_task else None
+        self._check(load().tcorr_energy_range(self._h, int(first), int(count), e, ptr))
+        return (tuple(e), et) if per_task else tuple(e)
+
+    def kernel_times(self, reset: bool = False):
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int64 * 4)()
+        self._check(load().tcorr_kernel_times(self._h, ms, n, 1 if reset else 0))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load().tcorr_device_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tcorr_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def num_tasks(o: int) -> int:
+    return o * (o + 1) * (o + 2) // 6
+
+
+def algorithmic_flops(o: int, v: int, ntasks: int | None = None) -> float:
+    """12 v^3 (v + o) per task with i, j, k not all equal (the six GEMM pairs
+    of the W contraction, Sec. 3); i = j = k tasks carry no work."""
+    if ntasks is None:
+        ntasks = num_tasks(o) - o
+    return 12.0 * v ** 3 * (v + o) * ntasks
