@@ -1,0 +1,379 @@
+"""Benchmark of the (T) triples-correction energy on GB300.
+
+Workload: the FP64 (T) energy of a synthetic alanine-chain-sized problem,
+o = 50 occupied, v = 450 virtual, naux = 1500, seed 2 (the seeded generator of
+paper_1609_08094_gb300.synth; vvvo alone is 36.5 GB FP64, resident in HBM).
+The full problem has C(52,3) = 22100 tasks (sorted occupied triples,
+Sec. 3) of equal weight (Sec. 5); a step is one pass of the whole hot path
+(W contractions, fused epilogue, reductions) over a contiguous batch of
+tasks, and throughput is reported in algorithmic TFLOP/s
+(12 v^3 (v+o) per task with i, j, k not all equal) and triples/s.
+
+One JSON line (rank 0) carries: the device-timed value, the end-to-end value
+through the C ABI with host buffers (copies inside the timed region), the
+roofline of the dominant kernel, the oracle timed on the host cores on a
+sample of the same workload, clocks sampled during the timed region, the
+mixed-precision (TF32x3 / BF16x3) results on the same sizes when the
+tensor-core path is available, and their errors against the FP64 path.
+
+`--impl reference` times the CPU oracle instead (the reference arm).
+Under torchrun each rank processes its own batch of tasks (weak scaling, no
+collective on the data path; the harness reduces timings with max).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "(T) TFLOP/s, triples/s: FP64 vs mixed at ≤1e-6 rel ΔE; serving p50/p99 latency"
+WORKLOAD = dict(o=50, v=450, naux=1500, seed=2)
+FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (152 SMs x 2070 MHz x 2 DFMA/clk x 2 flop)
+FP64_PROBE_TFLOPS = 1.20     # DFMA throughput probe on this machine's GB300
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tasks-per-step", type=int, default=4)
+    ap.add_argument("--mixed-tasks-per-step", type=int, default=64)
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-tasks", type=int, default=1)
+    ap.add_argument("--o", type=int, default=WORKLOAD["o"])
+    ap.add_argument("--v", type=int, default=WORKLOAD["v"])
+    ap.add_argument("--naux", type=int, default=WORKLOAD["naux"])
+    ap.add_argument("--seed", type=int, default=WORKLOAD["seed"])
+    return ap.parse_args()
+
+
+def sorted_tasks(o):
+    return [(i, j, k) for i in range(o) for j in range(i, o) for k in range(j, o)]
+
+
+def work_tasks(tasks, first, count):
+    return sum(1 for t in tasks[first:first + count] if not (t[0] == t[1] == t[2]))
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms in the background."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                rows.append((float(f[0]), float(f[1]), f[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def dist_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    import torch
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        torch.cuda.synchronize()
+
+
+def time_steps(t, tasks, first_fn, count, warmup, steps, world, stream):
+    """Device time (ms) of `steps` energy_range calls after `warmup` untimed."""
+    import torch
+    for w in range(warmup):
+        t.energy_range(first_fn(w), count)
+    t.kernel_times(reset=True)
+    barrier(world)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = []
+    for s in range(steps):
+        results.append(t.energy_range(first_fn(warmup + s), count))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    barrier(world)
+    return ms, results, t.kernel_times(reset=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import numpy as np
+    import torch
+
+    import oracle
+    import __graft_entry__
+    from paper_1609_08094_gb300 import synth, tcorr
+
+    rank, world, local = dist_setup(args)
+    __graft_entry__.build() if rank == 0 else None
+    if world > 1:
+        barrier(world)
+    tcorr.load()
+    o, v, naux, seed = args.o, args.v, args.naux, args.seed
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.time()
+    inst = synth.make_instance(o, v, naux, seed, device=dev)
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    tasks = sorted_tasks(o)
+    ntask = len(tasks)
+    fl_task = 12.0 * v ** 3 * (v + o)
+    K, W, C = args.steps, args.warmup, args.tasks_per_step
+    # rank r, step s: a contiguous batch of C tasks (weak scaling over ranks)
+    span = (W + K) * C
+
+    def first_of(s):
+        return ((rank * span + s * C) % max(1, ntask - C))
+
+    # ---- FP64, device-resident inputs -------------------------------------
+    t = tcorr.Tcorr.from_instance(inst, prec="fp64", profile=True, stream=stream)
+    with ClockSampler(local) as cs:
+        ms, res, ktimes = time_steps(t, tasks, first_of, C, W, K, world, stream)
+    clocks = cs.summary()
+    ms = dist_max(ms, world)
+    work = sum(work_tasks(tasks, first_of(W + s), C) for s in range(K))
+    all_work = dist_max(work, world) * world if world > 1 else work
+    value = all_work * fl_task / (ms * 1e-3) / 1e12
+    triples_s = (K * C * world) / (ms * 1e-3)
+    gemm_ms, gemm_n = ktimes["gemm"]
+    gemm_flops_per_launch = work * fl_task / max(1, gemm_n)
+    achieved = gemm_flops_per_launch / (gemm_ms / max(1, gemm_n) * 1e-3) / 1e12
+    launches = sum(n for _, n in ktimes.values())
+    shares = {k: round(m / max(1e-9, sum(mm for mm, _ in ktimes.values())), 4) for k, (m, _) in ktimes.items()}
+
+    # parity of the timed tasks against the oracle on a sample (rank 0)
+    parity = None
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        sample = [n for n in range(first_of(W), first_of(W) + C)
+                  if not (tasks[n][0] == tasks[n][1] == tasks[n][2])][: args.cpu_tasks]
+        need = sorted({q for n in sample for q in tasks[n]})
+        host = synth.Instance(o, v, naux, seed, inst.eps_occ.cpu().numpy(), inst.eps_vir.cpu().numpy(),
+                              inst.t1.cpu().numpy(), inst.t2.cpu().numpy(), None,
+                              inst.ooov.cpu().numpy(), inst.ovov.cpu().numpy())
+        slices = {q: inst.vvvo[:, :, :, q].contiguous().cpu().numpy() for q in need}
+        oracle.build()
+        threads = oracle.max_threads()
+        tc0 = time.time()
+        ref = oracle.triple_energies(host, np.array([tasks[n] for n in sample]), threads, slices=slices)
+        cpu_s = time.time() - tc0
+        _, per = t.energy_range(sample[0], sample[-1] - sample[0] + 1, per_task=True)
+        got = per[[n - sample[0] for n in sample]]
+        rel = float(np.max(np.abs(got.sum(1) - ref.sum(1)) / np.abs(ref.sum(1))))
+        parity = {"tasks": [list(tasks[n]) for n in sample], "max_rel_err_fp64": rel,
+                  "tol": 1e-10}
+        cpu = {"value": len(sample) * fl_task / cpu_s / 1e12, "unit": "TFLOP/s", "cores": threads,
+               "kind": "oracle", "sample": f"{len(sample)} tasks {[list(tasks[n]) for n in sample]} "
+                                          f"of the o={o}, v={v} workload ({cpu_s:.1f} s)",
+               "triples_per_s": len(sample) / cpu_s}
+        del host, slices
+    t.close()
+
+    # ---- mixed precision on the same sizes --------------------------------
+    mixed = {}
+    if not args.no_mixed:
+        for prec in ("tf32x3", "bf16x3"):
+            try:
+                tm = tcorr.Tcorr.from_instance(inst, prec=prec, profile=True, stream=stream)
+            except tcorr.TcorrError as e:
+                mixed[prec] = {"unavailable": str(e)}
+                continue
+            Cm = args.mixed_tasks_per_step
+
+            def first_m(s, Cm=Cm):
+                return ((rank * (W + K) * Cm + s * Cm) % max(1, ntask - Cm))
+            msm, resm, kt = time_steps(tm, tasks, first_m, Cm, W, K, world, stream)
+            msm = dist_max(msm, world)
+            workm = sum(work_tasks(tasks, first_m(W + s), Cm) for s in range(K))
+            gm, gn = kt["gemm"]
+            ent = {"value": workm * world * fl_task / (msm * 1e-3) / 1e12, "unit": "TFLOP/s",
+                   "triples_per_s": K * Cm * world / (msm * 1e-3), "ms_per_step": msm / K,
+                   "tasks_per_step": Cm,
+                   "kernel_ms_share": {k: round(m / max(1e-9, sum(mm for mm, _ in kt.values())), 4)
+                                       for k, (m, _) in kt.items()},
+                   "gemm_tflops": workm * fl_task / (gm * 1e-3) / 1e12 if gm > 0 else None}
+            # error vs the FP64 GPU path on the first timed batch
+            em = tm.energy_range(first_m(W), Cm)
+            tf = tcorr.Tcorr.from_instance(inst, prec="fp64", stream=stream)
+            ef = tf.energy_range(first_m(W), min(Cm, 8))
+            em8 = tm.energy_range(first_m(W), min(Cm, 8))
+            tf.close()
+            ent["rel_err_vs_fp64"] = abs(em8[2] - ef[2]) / abs(ef[2])
+            ent["speedup_vs_fp64"] = ent["value"] / value
+            mixed[prec] = ent
+            tm.close()
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    e2e = None
+    if not args.no_e2e:
+        arrays = [a.cpu().pin_memory() for a in inst.arrays()]
+        h2d = sum(a.numel() * 8 for a in arrays)
+        for _ in range(1):  # warm-up
+            with tcorr.Tcorr(o, v, *[a.numpy() for a in arrays], prec="fp64") as te:
+                te.energy_range(first_of(0), C)
+        barrier(world)
+        KE = max(1, min(K, 2))
+        te0 = time.perf_counter()
+        for s in range(KE):
+            with tcorr.Tcorr(o, v, *[a.numpy() for a in arrays], prec="fp64") as te:
+                te.energy_range(first_of(W + s), C)
+        torch.cuda.synchronize()
+        e_ms = dist_max((time.perf_counter() - te0) * 1e3, world)
+        worke = sum(work_tasks(tasks, first_of(W + s), C) for s in range(KE))
+        e2e = {"value": worke * world * fl_task / (e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24, "steps": KE,
+               "ms_per_step": e_ms / KE,
+               "note": "per step: tcorr_create from pinned host arrays (H2D + layout prep), "
+                       "tcorr_energy_range, 3-double result read, tcorr_destroy"}
+        del arrays
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"FP64 (T) energy, o={o} v={v} naux={naux} seed={seed}, "
+                               f"{C} tasks per step per GPU",
+                   "o": o, "v": v, "naux": naux, "seed": seed, "tasks_per_step": C,
+                   "tasks_total": ntask, "l2": "inputs larger than L2 (one vvvo slice is "
+                                                f"{v ** 3 * 8 / 1e6:.0f} MB FP64)",
+                   "generate_s": round(gen_s, 1)},
+        "triples_per_s": triples_s,
+        "roofline": {"bound": "alu", "kernel": "ugemm_f64_kernel", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": None,
+                     "peak_note": "nominal FP64 (no FP64 figure in the measured peaks); "
+                                  f"DFMA probe measured {FP64_PROBE_TFLOPS} TFLOP/s"},
+        "kernel_ms_share": shares,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "parity": parity,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "mixed": mixed,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def reference_arm(args):
+    """The oracle, as it stands, on the host cores: each step one task of the
+    same workload (tasks have equal weight)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1609_08094_gb300 import synth
+    o, v, naux, seed = args.o, args.v, args.naux, args.seed
+    tasks = [t for t in sorted_tasks(o) if not (t[0] == t[1] == t[2])]
+    K, W = args.steps, args.warmup
+    steps = [tasks[(97 * s) % len(tasks)] for s in range(W + K)][W:]
+    need = sorted({q for t in steps for q in t})
+    # only what the sampled tasks read: every block but vvvo, and vvvo slices
+    inst, slices = synth.make_instance_slices(o, v, naux, seed, need)
+    oracle.build()
+    threads = oracle.max_threads()
+    fl_task = 12.0 * v ** 3 * (v + o)
+    # warm-up steps warm the process (library load, thread pool) on a small
+    # instance; a full-size task takes tens of seconds on the host
+    small = synth.make_instance(4, 20, 72, 1)
+    for s in range(W):
+        oracle.triple_energies(small, np.array([[0, 1, 2]]), threads)
+    t0 = time.perf_counter()
+    for s in range(K):
+        oracle.triple_energies(inst, np.array([steps[s]]), threads, slices=slices)
+    sec = time.perf_counter() - t0
+    value = K * fl_task / sec / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": K, "warmup": W,
+            "ms_per_step": sec * 1e3 / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"FP64 (T) energy, o={o} v={v} naux={naux} seed={seed}, "
+                                   "1 task per step (CPU oracle)", "o": o, "v": v},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                             "sample": f"one task per step of the o={o}, v={v} workload"},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -15,7 +15,7 @@ constexpr int TT = 32;  // transpose tile edge
 __device__ __forceinline__ float tf32_rn(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float(r & 0xFFFFE000u);  // TF32 keeps 10 mantissa bits
 }
 
 template <int KIND>

@@ -60,8 +60,10 @@ void release(Handle &h) {
         if (p) cudaFree(p);
     if (h.h_sums) cudaFreeHost(h.h_sums);
     if (h.h_err) cudaFreeHost(h.h_err);
-    for (auto &e : h.ev)
-        if (e) cudaEventDestroy(e);
+    for (auto &pe : h.pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
     free(h.tmaps);
     h = Handle();
 }
@@ -87,30 +89,38 @@ void free_tmp(Handle &h, double *&tmp, size_t n) {
 struct Timer {
     Handle &h;
     int cls;
-    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEvent_t a = nullptr;
     Timer(Handle &hh, int c) : h(hh), cls(c) {
         if (!h.profile) return;
         CK(cudaEventCreate(&a));
-        CK(cudaEventCreate(&b));
         CK(cudaEventRecord(a, h.stream));
     }
     void stop() {
-        if (!h.profile) return;
+        if (!h.profile || !a) return;
+        cudaEvent_t b = nullptr;
+        CK(cudaEventCreate(&b));
         CK(cudaEventRecord(b, h.stream));
-        CK(cudaEventSynchronize(b));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, a, b));
-        h.k_ms[cls] += ms;
-        h.k_launch[cls] += 1;
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-        a = b = nullptr;
+        h.pending.push_back({cls, a, b});
+        a = nullptr;
     }
     ~Timer() {
         if (a) cudaEventDestroy(a);
-        if (b) cudaEventDestroy(b);
     }
 };
+
+// Accumulate the recorded event pairs; call after a stream synchronisation.
+void resolve_timers(Handle &h) {
+    for (auto &pe : h.pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+            h.k_ms[pe.cls] += ms;
+            h.k_launch[pe.cls] += 1;
+        }
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    h.pending.clear();
+}
 
 int elem_kind(int prec) { return prec == TCORR_FP64 ? 0 : (prec == TCORR_TF32X3 ? 1 : 2); }
 size_t elem_bytes(int prec) { return prec == TCORR_FP64 ? 8 : (prec == TCORR_TF32X3 ? 4 : 2); }
@@ -296,6 +306,7 @@ void run_range(Handle &h, int64_t first, int64_t count, double *e_out, double *e
         CK(cudaMemcpyAsync(e_task, h.task_e + 2 * first, (size_t)count * 2 * sizeof(double),
                            cudaMemcpyDeviceToHost, h.stream));
     CK(cudaStreamSynchronize(h.stream));
+    resolve_timers(h);
     check_err_flag(h);
     e_out[0] = h.h_sums[0];
     e_out[1] = h.h_sums[1];
@@ -407,6 +418,7 @@ tcorr_status tcorr_create(tcorr_t *out, int o, int v, const double *eps_occ,
         }
         CK(cudaStreamSynchronize(h.stream));
         CK(cudaGetLastError());
+        resolve_timers(h);
     } catch (const Fail &f) {
         g_create_error = f.msg;
         cudaStreamSynchronize(h.stream);

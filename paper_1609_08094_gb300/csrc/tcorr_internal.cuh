@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/tcorr.h"
 
@@ -82,8 +83,10 @@ struct Handle {
     // tcgen05 path
     void *tmaps = nullptr;   // host-side tensor maps (CUtensorMap array), built at create
 
-    // profiling
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    // profiling: event pairs recorded around launches, resolved after the
+    // call's final stream synchronisation (no sync inside the launch sequence)
+    struct Pending { int cls; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
     double k_ms[KC_COUNT] = {0, 0, 0, 0};
     int64_t k_launch[KC_COUNT] = {0, 0, 0, 0};
 

@@ -197,6 +197,32 @@ def make_instance(o: int, v: int, naux: int | None = None, seed: int = 1,
                     vvvo.contiguous(), ooov.contiguous(), ovov.contiguous())
 
 
+def make_instance_slices(o: int, v: int, naux: int | None, seed: int, occ):
+    """The instance of make_instance(o, v, naux, seed) on the host without the
+    full vvvo block (vvvo=None), plus {q: (xy|zq) as [v][v][v]} for the
+    occupied indices in ``occ`` -- what a sample of tasks reads."""
+    if naux is None:
+        naux = 3 * (o + v)
+    B = factors(o, v, naux, seed)
+    eo, ev = orbital_energies(o, v, seed)
+    t1 = singles(o, v, seed)
+    Bov = np.ascontiguousarray(B[:, :o, o:])
+    Boo = np.ascontiguousarray(B[:, :o, :o])
+    Bvv = np.ascontiguousarray(B[:, o:, o:]).reshape(naux, v * v)
+    del B
+    Xov = Bov.reshape(naux, o * v)
+    ovov = (Xov.T @ Xov).reshape(o, v, o, v)
+    ooov = (Boo.reshape(naux, o * o).T @ Xov).reshape(o, o, o, v)
+    dd = (eo[:, None, None, None] + eo[None, None, :, None]
+          - ev[None, :, None, None] - ev[None, None, None, :])
+    t2 = np.ascontiguousarray((ovov / dd).transpose(0, 2, 1, 3))
+    slices = {}
+    for q in sorted(set(int(x) for x in occ)):
+        Bvq = np.ascontiguousarray(Bov[:, q, :])                      # [Q][z] = B^Q_{zq}
+        slices[q] = (Bvv.T @ Bvq).reshape(v, v, v)
+    return Instance(o, v, naux, seed, eo, ev, t1, t2, None, ooov, ovov), slices
+
+
 def batch_shapes(n: int, seed: int, o_range=(4, 16), v_range=(20, 120)):
     """(o, v, naux, seed) for n independent molecules of uneven size:
     o ~ U{o_range}, v ~ U{v_range} (inclusive), naux = 3(o+v), per-instance

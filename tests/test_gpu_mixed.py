@@ -1,0 +1,74 @@
+"""Tensor-core (tcgen05) mixed-precision path against the CPU oracle, through
+the C ABI (GPU).  Tolerance: 1e-6 relative on E(T) (Sec. 4 accepts 1e-6 a.u.
+for mixed precision); the achieved error is printed."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1609_08094_gb300 import synth, tcorr
+
+pytestmark = pytest.mark.gpu
+MIXED_TOL = 1e-6
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1609_08094_gb300 import _build
+    _build.build()
+    oracle.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def energy(inst, prec, **kw):
+    dev = inst.to("cuda")
+    with tcorr.Tcorr.from_instance(dev, prec=prec, **kw) as t:
+        return t.energy()
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("o,v,naux,seed", [
+    (4, 20, 72, 1),      # small configuration (o=4, v=20, naux=72)
+    (3, 16, None, 2), (2, 33, None, 3), (5, 47, None, 4), (3, 130, None, 5),
+    (6, 64, None, 6), (2, 270, None, 7),
+])
+def test_mixed_matches_oracle(prec, o, v, naux, seed):
+    inst = synth.make_instance(o, v, naux, seed)
+    ref = oracle.energy(inst)
+    got = energy(inst, prec)
+    err = rel(got[2], ref[2])
+    print(f"{prec} o={o} v={v}: rel err E(T) {err:.2e}, E4 {rel(got[0], ref[0]):.2e}")
+    assert err <= MIXED_TOL, (prec, got, ref)
+    assert rel(got[0], ref[0]) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_mixed_per_task(prec):
+    inst = synth.make_instance(4, 37, None, 21)
+    tasks = oracle.sorted_triples(4)
+    ref = oracle.triple_energies(inst, tasks)
+    with tcorr.Tcorr.from_instance(inst.to("cuda"), prec=prec, batch_tasks=3) as t:
+        _, per = t.energy_range(0, t.num_tasks, per_task=True)
+        e1 = t.energy()
+        e2 = t.energy()
+    assert e1 == e2  # deterministic (no atomics)
+    tot = per.sum(1)
+    rt = ref.sum(1)
+    scale = np.abs(rt).max()
+    assert np.all(np.abs(tot - rt) <= 1e-6 * scale)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_mixed_edge_cases(prec):
+    # single occupied: every task is i=j=k, exact zero
+    inst = synth.make_instance(1, 24, None, 3)
+    assert energy(inst, prec) == (0.0, 0.0, 0.0)
+    # zero singles: E5 exactly zero
+    inst = synth.make_instance(3, 20, None, 4)
+    inst.t1 = np.zeros_like(inst.t1)
+    e4, e5, e = energy(inst, prec)
+    assert e5 == 0.0 and e == e4
