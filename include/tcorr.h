@@ -141,6 +141,40 @@ const char *tcorr_status_string(tcorr_status s);
 /* ABI version (incremented on incompatible change). */
 int tcorr_version(void);
 
+/*
+ * Allocation-free variant (the paper has no counterpart; it exists for
+ * callers that must not allocate device memory: applications whose device
+ * memory is owned entirely by their own pool or budget, and latency-sensitive
+ * loops that cannot afford cudaMalloc/cudaFree, which synchronise the device).
+ *
+ * E[4] and E[5] share of one task (i <= j <= k) in FP64, computed from the
+ * caller's canonical device arrays (same layouts as tcorr_create, device
+ * pointers only), written to e_out (device pointer, 2 doubles).  Every
+ * intermediate lives in one fixed file-scope device array of
+ * TCORR_NOALLOC_SCRATCH_BYTES that each GPU loading the library holds until
+ * the process exits; no call allocates or frees memory.
+ *  - Sizes: 1 <= v <= TCORR_NOALLOC_MAX_V, 1 <= o <= 4096; anything else,
+ *    a NULL pointer or an unsorted/out-of-range task returns EINVAL before
+ *    any device work.
+ *  - The first call on a device resolves the scratch address for that device
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - Asynchronous on stream (NULL = legacy default stream): e_out is valid
+ *    once the stream has been synchronised.
+ *  - The scratch is shared by every call on a device and keeps the last
+ *    call's contents (nothing in it needs to start at zero).  Calls that
+ *    overlap on the GPU (other streams, other host threads) race on it:
+ *    serialise them.
+ */
+#define TCORR_NOALLOC_MAX_V 64
+#define TCORR_NOALLOC_SCRATCH_BYTES 6295552
+tcorr_status tcorr_task_energy_noalloc(int o, int v, const double *eps_occ,
+                                       const double *eps_vir, const double *t1,
+                                       const double *t2, const double *vvvo,
+                                       const double *ooov, const double *ovov,
+                                       int i, int j, int k, double *e_out,
+                                       void *stream);
+
 #ifdef __cplusplus
 }
 #endif

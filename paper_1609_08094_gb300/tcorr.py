@@ -75,13 +75,18 @@ def load():
         lib.tcorr_status_string.argtypes = [ctypes.c_int]
         lib.tcorr_version.restype = ctypes.c_int
         lib.tcorr_version.argtypes = []
+        lib.tcorr_task_energy_noalloc.restype = ctypes.c_int
+        lib.tcorr_task_energy_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp,
+                                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
         _lib = lib
         return lib
 
 
 EXPORTS = ("tcorr_create", "tcorr_energy", "tcorr_energy_range", "tcorr_num_tasks",
            "tcorr_task", "tcorr_kernel_times", "tcorr_device_bytes", "tcorr_destroy",
-           "tcorr_last_error", "tcorr_status_string", "tcorr_version")
+           "tcorr_last_error", "tcorr_status_string", "tcorr_version",
+           "tcorr_task_energy_noalloc")
+NOALLOC_MAX_V = 64
 
 
 def _shape_check(name, a, shape):
@@ -200,6 +205,29 @@ class Tcorr:
             self.close()
         except Exception:
             pass
+
+
+def task_energy_noalloc(o, v, eps_occ, eps_vir, t1, t2, vvvo, ooov, ovov, ijk, out, stream=None):
+    """FP64 (E[4], E[5]) share of one task into ``out`` (a float64 CUDA tensor
+    of 2 elements) without any device allocation by the library: for callers
+    whose device memory is owned by their own pool or budget, or that cannot
+    pay cudaMalloc's device synchronisation.  Uses a fixed device scratch
+    array (v <= NOALLOC_MAX_V); asynchronous on ``stream``.  Calls that overlap
+    on the GPU race on the shared scratch; the first call on a device must
+    precede any stream capture."""
+    import torch
+    arrays = dict(eps_occ=eps_occ, eps_vir=eps_vir, t1=t1, t2=t2, vvvo=vvvo, ooov=ooov, ovov=ovov)
+    ptrs = [_pointer(k, a, True) for k, a in arrays.items()]
+    if out.dtype != torch.float64 or not out.is_cuda or out.numel() < 2:
+        raise ValueError("out: needs a float64 CUDA tensor with 2 elements")
+    if stream is None:
+        stream = torch.cuda.current_stream(out.device)
+    sptr = getattr(stream, "cuda_stream", stream) or 0
+    i, j, k = (int(x) for x in ijk)
+    st = load().tcorr_task_energy_noalloc(int(o), int(v), *ptrs, i, j, k, out.data_ptr(),
+                                          ctypes.c_void_p(sptr))
+    if st != 0:
+        raise TcorrError(st, "tcorr_task_energy_noalloc rejected the call")
 
 
 def num_tasks(o: int) -> int:
