@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--tasks-per-step", type=int, default=4)
     ap.add_argument("--mixed-tasks-per-step", type=int, default=64)
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--precs", default="tf32x3,bf16x3", help="mixed precisions to time")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-tasks", type=int, default=1)
@@ -248,7 +249,7 @@ def main():
     # ---- mixed precision on the same sizes --------------------------------
     mixed = {}
     if not args.no_mixed:
-        for prec in ("tf32x3", "bf16x3"):
+        for prec in [x for x in args.precs.split(",") if x]:
             try:
                 tm = tcorr.Tcorr.from_instance(inst, prec=prec, profile=True, stream=stream)
             except tcorr.TcorrError as e:

@@ -179,6 +179,183 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const EpiParams p) {
     }
 }
 
+
+// Mixed-precision epilogue: the same block-orbit algorithm with 8^3 cubes in
+// FP32, sized for occupancy (about 20 KB of shared memory, 8 CTAs per SM).
+// The Y operands of the orbit (t1 rows and the three ovov sub-blocks) and
+// the block-relative virtual energies are staged in shared memory.  The
+// denominator of element (x,y,z) is base + d[x] + d[y] + d[z] with
+// base = e_i+e_j+e_k - e_A0 - e_B0 - e_C0 formed in FP64 once per CTA (it is
+// the same for all six cubes of an orbit) and rounded to FP32 once, and
+// d[x] = e_X0 - e_x the FP32 offset from x's block origin.  Element terms
+// are summed in FP32 per thread and warp, and in FP64 (Kahan) across warps.
+constexpr int F8 = 8;
+constexpr int FP0 = 69, FP1 = 8;    // plane / row pitch of a cube: at most 2-way bank conflicts
+constexpr int FSLOT = F8 * FP0;     // floats per cube slot
+
+__global__ void __launch_bounds__(NT) epilogue_f32_kernel(const EpiParams p) {
+    __shared__ float Ws[6 * FSLOT];
+    __shared__ float T1s[3][3][F8];          // [occupied i,j,k][orbit block][local]
+    __shared__ float OVs[3][3][3][F8 * F8];  // [(jk),(ik),(ij)][block][block][8x8]
+    __shared__ float Dls[3][F8];             // [orbit block][local] block-relative energies
+    __shared__ float base_s;
+    __shared__ int comp[6][6];
+    __shared__ int pos[6][3];                // orbit position (0,1,2 = A,B,C) of each cube dim
+    __shared__ int distinct[6];
+    __shared__ int ob[3];
+    __shared__ double red[NT / 32][2];
+
+    const int o = p.dm.o, v = p.dm.v, vc = p.dm.vc;
+    const int64_t v2 = (int64_t)v * v;
+    const int orb = blockIdx.x, tb = blockIdx.y, tid = threadIdx.x;
+    const int *tk = p.tasks + 3 * (p.task0 + tb);
+    const int ti = tk[0], tj = tk[1], tkk = tk[2];
+    double *out = p.partials + ((int64_t)tb * p.norb + orb) * 2;
+    if (ti == tj && tj == tkk) {
+        if (tid == 0) { out[0] = 0.0; out[1] = 0.0; }
+        return;
+    }
+    const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    if (tid < 36) {
+        const int pi = tid / 6, q = tid % 6;
+        const int t0 = P[pi][P[q][0]], t1v = P[pi][P[q][1]], t2v = P[pi][P[q][2]];
+        int sig = 0;
+        for (int s = 0; s < 6; s++)
+            if (P[s][0] == t0 && P[s][1] == t1v && P[s][2] == t2v) sig = s;
+        comp[pi][q] = sig;
+    }
+    if (tid < 3) ob[tid] = p.orbits[3 * orb + tid];
+    if (tid >= 64 && tid < 70) {
+        const int s = tid - 64;
+        pos[s][0] = P[s][0];
+        pos[s][1] = P[s][1];
+        pos[s][2] = P[s][2];
+    }
+    __syncthreads();
+    if (tid < 6) {
+        int d = 1;
+        for (int s = 0; s < tid; s++)
+            if (ob[P[s][0]] == ob[P[tid][0]] && ob[P[s][1]] == ob[P[tid][1]] && ob[P[s][2]] == ob[P[tid][2]]) d = 0;
+        distinct[tid] = d;
+    }
+    if (tid == 96) {
+        const double eijk = p.eps_o[ti] + p.eps_o[tj] + p.eps_o[tkk];
+        base_s = (float)(eijk - p.eps_v[ob[0] * F8] - p.eps_v[ob[1] * F8] - p.eps_v[ob[2] * F8]);
+    }
+    // stage t1, ovov sub-blocks and block-relative energies
+    const float *t1 = static_cast<const float *>(p.t1);
+    const float *ov = static_cast<const float *>(p.ovov);
+    for (int e = tid; e < 3 * 3 * F8; e += NT) {
+        const int oc = e / (3 * F8), b = (e / F8) % 3, m = e % F8;
+        const int x = ob[b] * F8 + m;
+        const int occ = oc == 0 ? ti : (oc == 1 ? tj : tkk);
+        T1s[oc][b][m] = x < v ? t1[occ * v + x] : 0.f;
+    }
+    for (int e = tid; e < 3 * F8; e += NT) {
+        const int b = e / F8, m = e % F8, x = ob[b] * F8 + m;
+        Dls[b][m] = x < v ? p.dev_f[x] : 0.f;
+    }
+    // slices: 0 = (j y | k z), 1 = (i x | k z), 2 = (i x | j y)
+    for (int e = tid; e < 3 * 9 * F8 * F8; e += NT) {
+        const int sl = e / (9 * 64), bb = (e / 64) % 9, m = (e / 8) % 8, n = e % 8;
+        const int ba = bb / 3, bc = bb % 3;
+        const int r = ob[ba] * F8 + m, c = ob[bc] * F8 + n;
+        const int first = sl == 0 ? tj : ti, second = sl == 2 ? tj : tkk;
+        float val = 0.f;
+        if (r < v && c < v) val = ov[(((int64_t)first * v + r) * o + second) * v + c];
+        OVs[sl][ba][bc][m * F8 + n] = val;
+    }
+
+    // W[x][y][z] = S0[x][y][z] + S1[x][y][z] + S2[z][x][y]: slots 0 and 1 read
+    // along z, slot 2 along y (all rows contiguous); all float4 loads of a
+    // thread are issued before any use.
+    const float *S0 = static_cast<const float *>(p.U) + (int64_t)(tb * 3 + 0) * v2 * vc;
+    const int64_t gs = v2 * vc;
+    float4 ra[3], rb[3], rc[3];
+#pragma unroll
+    for (int it = 0; it < 3; it++) {
+        const int idx = tid + it * NT;            // 6 slots x 64 rows x 2 halves = 768
+        const int s = idx >> 7, row = (idx >> 1) & 63, hf = idx & 1;
+        // slots 0,1: row (x, y), 4 values of z
+        const int x = ob[pos[s][0]] * F8 + (row >> 3), y = ob[pos[s][1]] * F8 + (row & 7);
+        const int z0 = ob[pos[s][2]] * F8 + hf * 4;
+        ra[it] = rb[it] = rc[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (x < v && y < v && z0 < v) {
+            const float4 *q = reinterpret_cast<const float4 *>(S0 + ((int64_t)x * v + y) * vc + z0);
+            ra[it] = __ldg(q);
+            rb[it] = __ldg(q + gs / 4);
+        }
+        // slot 2: row (z, x), 4 values of y
+        const int z = ob[pos[s][2]] * F8 + (row >> 3), x2 = ob[pos[s][0]] * F8 + (row & 7);
+        const int y0 = ob[pos[s][1]] * F8 + hf * 4;
+        if (z < v && x2 < v && y0 < v)
+            rc[it] = __ldg(reinterpret_cast<const float4 *>(S0 + 2 * gs + ((int64_t)z * v + x2) * vc + y0));
+    }
+#pragma unroll
+    for (int it = 0; it < 3; it++) {
+        const int idx = tid + it * NT;
+        const int s = idx >> 7, row = (idx >> 1) & 63, hf = idx & 1;
+        const int z0 = ob[pos[s][2]] * F8 + hf * 4;
+        float *wrow = Ws + s * FSLOT + (row >> 3) * FP0 + (row & 7) * FP1 + hf * 4;
+        const float w[4] = {ra[it].x + rb[it].x, ra[it].y + rb[it].y, ra[it].z + rb[it].z, ra[it].w + rb[it].w};
+#pragma unroll
+        for (int m = 0; m < 4; m++) wrow[m] = (z0 + m < v) ? w[m] : 0.f;  // U row padding is not data
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < 3; it++) {
+        const int idx = tid + it * NT;
+        const int s = idx >> 7, row = (idx >> 1) & 63, hf = idx & 1;
+        const int lz = row >> 3, lx = row & 7;
+        const int y0 = ob[pos[s][1]] * F8 + hf * 4;
+        const float w[4] = {rc[it].x, rc[it].y, rc[it].z, rc[it].w};
+#pragma unroll
+        for (int m = 0; m < 4; m++)
+            if (y0 + m < v) Ws[s * FSLOT + lx * FP0 + (hf * 4 + m) * FP1 + lz] += w[m];
+    }
+    __syncthreads();
+
+    const float base = base_s;
+    float a4 = 0.f, a5 = 0.f;
+    for (int s = 0; s < 6; s++) {
+        if (!distinct[s]) continue;
+        const int p0 = pos[s][0], p1 = pos[s][1], p2 = pos[s][2];
+        // cube slots holding W at the five other orderings of this slot's indices
+        const float *W0 = Ws + comp[s][0] * FSLOT, *W1 = Ws + comp[s][1] * FSLOT;
+        const float *W2 = Ws + comp[s][2] * FSLOT, *W3 = Ws + comp[s][3] * FSLOT;
+        const float *W4 = Ws + comp[s][4] * FSLOT, *W5 = Ws + comp[s][5] * FSLOT;
+        for (int l = tid; l < 512; l += NT) {
+            const int l0 = l >> 6, l1 = (l >> 3) & 7, l2 = l & 7;
+            const int x = ob[p0] * F8 + l0, y = ob[p1] * F8 + l1, z = ob[p2] * F8 + l2;
+            if (x >= v || y >= v || z >= v) continue;
+            const float w0 = W0[l0 * FP0 + l1 * FP1 + l2];
+            // Z = 8 W(abc) - 4 (W(acb) + W(bac) + W(cba)) + 2 (W(bca) + W(cab))
+            const float zv = 8.f * w0 -
+                             4.f * (W1[l0 * FP0 + l2 * FP1 + l1] + W2[l1 * FP0 + l0 * FP1 + l2] +
+                                    W5[l2 * FP0 + l1 * FP1 + l0]) +
+                             2.f * (W3[l1 * FP0 + l2 * FP1 + l0] + W4[l2 * FP0 + l0 * FP1 + l1]);
+            const float yv = T1s[0][p0][l0] * OVs[0][p1][p2][l1 * F8 + l2] +
+                             T1s[1][p1][l1] * OVs[1][p0][p2][l0 * F8 + l2] +
+                             T1s[2][p2][l2] * OVs[2][p0][p1][l0 * F8 + l1];
+            const float r = __frcp_rn(base + (Dls[p0][l0] + Dls[p1][l1] + Dls[p2][l2]));
+            a4 = fmaf(zv * w0, r, a4);
+            a5 = fmaf(zv * yv, r, a5);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        a4 += __shfl_xor_sync(0xffffffffu, a4, off);
+        a5 += __shfl_xor_sync(0xffffffffu, a5, off);
+    }
+    if ((tid & 31) == 0) { red[tid >> 5][0] = (double)a4; red[tid >> 5][1] = (double)a5; }
+    __syncthreads();
+    if (tid == 0) {
+        double t4 = 0.0, k4 = 0.0, t5 = 0.0, k5 = 0.0;
+        for (int w = 0; w < NT / 32; w++) { kahan_add(t4, k4, red[w][0]); kahan_add(t5, k5, red[w][1]); }
+        out[0] = t4 - k4;
+        out[1] = t5 - k5;
+    }
+}
+
 // One CTA per task of the batch: Kahan sum of the orbit partials, times m/6.
 __global__ void __launch_bounds__(NT) task_reduce_kernel(const int *tasks, int64_t task0, int norb,
                                                          const double *partials, double *task_e) {
@@ -261,8 +438,10 @@ cudaError_t launch_epilogue(int prec, const EpiArgs &ea, cudaStream_t st) {
         if (ea.te != 8) return cudaErrorInvalidValue;
         return launch_epi_t<double, double, 8>(p, ea.ntb, st);
     }
-    if (ea.te != 16) return cudaErrorInvalidValue;
-    return launch_epi_t<float, float, 16>(p, ea.ntb, st);
+    if (ea.te != F8) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)p.norb, (unsigned)ea.ntb);
+    epilogue_f32_kernel<<<grid, NT, 0, st>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_task_reduce(const EpiArgs &ea, cudaStream_t st) {

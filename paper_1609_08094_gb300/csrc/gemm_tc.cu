@@ -12,11 +12,12 @@
 // FP32 accumulator with truncation, so a long chain of MMAs into one
 // accumulator shrinks |U| systematically (relative bias ~ number of chained
 // instructions x 2^-24; Ootomo & Yokota 2022 recover FP32 accuracy by
-// accumulating outside the tensor core).  Here the dominant hi*hi product is
-// accumulated per K block of KB chunks into a fresh TMEM accumulator H and
-// folded into a register-resident total with round-to-nearest FP32 adds;
-// the small hi*lo + lo*hi corrections (2^-11 of the total) run in a second
-// accumulator C over the whole K range.
+// accumulating outside the tensor core).  Here the three products of each
+// K block of KB chunks go into a fresh TMEM accumulator, and the epilogue
+// warps fold every block into a register-resident total with
+// round-to-nearest FP32 adds.  The block accumulator is double-buffered
+// (H0 = TMEM columns [0,256), H1 = [256,512)), so the MMAs of block n+1 run
+// while block n is drained.
 //
 // Kernel structure (one persistent CTA per SM, 10 warps):
 //   warp 0  : TMA producer.  Per K chunk it loads A_hi, A_lo (128 pair rows
@@ -25,12 +26,12 @@
 //             strides, so the tile rows always come out in (b,c) order) and
 //             B_hi, B_lo (up to 256 rows of a) into a 4-stage ring, 64-byte
 //             swizzled rows.
-//   warp 1  : allocates 512 TMEM columns (H = [0,256), C = [256,512)); one
-//             thread issues tcgen05.mma (M = 128, N <= 256, 2 K-steps per
-//             chunk): hi*hi into H, then hi*lo and lo*hi into C.
-//   warps 2-9: two warps per TMEM lane quarter, 128 columns each: drain H
-//             after every K block into the register total, add C at the end
-//             of the tile and store the U rows.
+//   warp 1  : allocates 512 TMEM columns; one thread issues tcgen05.mma
+//             (M = 128, N <= 256, 2 K-steps x 3 products per chunk) into the
+//             block accumulator of the current K block.
+//   warps 2-9: two warps per TMEM lane quarter, 128 columns each: drain each
+//             block into the register total, then store the U rows (rows of
+//             16 consecutive c, coalesced) at the end of the tile.
 // A work item is (task, group, pair tile, N pass of 256 a values).  Every
 // mbarrier wait is bounded (wall clock): on expiry the kernel sets an error
 // flag, stops all roles, waits (bounded) for its own copies in flight, frees
@@ -214,7 +215,7 @@ template <int KIND>
 __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_constant__ TcParams p) {
     extern __shared__ __align__(1024) uint8_t smem_dyn[];
     __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
-    __shared__ __align__(8) uint64_t bar_hfull, bar_hempty, bar_cfull, bar_cempty;
+    __shared__ __align__(8) uint64_t bar_hfull[2], bar_hempty[2];
     __shared__ uint32_t tmem_holder;
     __shared__ volatile int abort_sh;
 
@@ -226,10 +227,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
             mbar_init(smem_u32(&bar_full[s]), 1);
             mbar_init(smem_u32(&bar_empty[s]), 1);
         }
-        mbar_init(smem_u32(&bar_hfull), 1);
-        mbar_init(smem_u32(&bar_hempty), EPI_THREADS);
-        mbar_init(smem_u32(&bar_cfull), 1);
-        mbar_init(smem_u32(&bar_cempty), EPI_THREADS);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(smem_u32(&bar_hfull[b]), 1);
+            mbar_init(smem_u32(&bar_hempty[b]), EPI_THREADS);
+        }
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_holder;
-    const uint32_t tmem_h = tmem, tmem_c = tmem + (uint32_t)BN;
+
     const int v = p.dm.v, o = p.dm.o;
     const int nch = 2 * p.kv + 2 * p.ko;
     const int kch = ROW_BYTES / (KIND == 1 ? 4 : 2);
@@ -308,8 +309,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t hblk = 0;   // H blocks issued so far (phase counter)
-            uint32_t local = 0;  // tiles issued so far (C phase counter)
+            uint32_t hblk = 0;  // K blocks issued so far: buffer hblk & 1, phase (hblk >> 1) & 1
             bool ok = true;
             for (int64_t it = blockIdx.x; it < p.nitems && ok; it += gridDim.x) {
                 const Item w = decode(p, it);
@@ -328,42 +328,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                     }
                     const bool hfirst = (ch % p.kb) == 0;
                     const bool hlast = ((ch + 1) % p.kb) == 0 || ch == nch - 1;
-                    if (hfirst && !mbar_wait(smem_u32(&bar_hempty), (hblk & 1u) ^ 1u, &abort_sh)) {
-                        fail(&abort_sh, p.err, DERR_TIMEOUT_TMEM);
-                        ok = false;
-                        break;
-                    }
-                    if (ch == 0 && !mbar_wait(smem_u32(&bar_cempty), (local & 1u) ^ 1u, &abort_sh)) {
+                    const uint32_t buf = hblk & 1u;
+                    if (hfirst &&
+                        !mbar_wait(smem_u32(&bar_hempty[buf]), ((hblk >> 1) & 1u) ^ 1u, &abort_sh)) {
                         fail(&abort_sh, p.err, DERR_TIMEOUT_TMEM);
                         ok = false;
                         break;
                     }
                     tc_fence_after();
+                    const uint32_t d = tmem + buf * (uint32_t)BN;
                     const uint32_t sA = sbase + stage * STAGE_BYTES, sAl = sA + A_BYTES;
                     const uint32_t sB = sAl + A_BYTES, sBl = sB + B_BYTES;
 #pragma unroll
                     for (int kk = 0; kk < 2; kk++) {
                         const uint32_t off = kk * 32;
-                        tc_mma<KIND>(tmem_h, sdesc(sA + off), sdesc(sB + off), idesc,
-                                     (!hfirst || kk > 0) ? 1u : 0u);
-                    }
-                    if (hlast) {
-                        tc_commit(smem_u32(&bar_hfull));
-                        hblk++;
-                    }
-#pragma unroll
-                    for (int kk = 0; kk < 2; kk++) {
-                        const uint32_t off = kk * 32;
-                        tc_mma<KIND>(tmem_c, sdesc(sA + off), sdesc(sBl + off), idesc,
-                                     (ch > 0 || kk > 0) ? 1u : 0u);
-                        tc_mma<KIND>(tmem_c, sdesc(sAl + off), sdesc(sB + off), idesc, 1u);
+                        const uint64_t ah = sdesc(sA + off), al = sdesc(sAl + off);
+                        const uint64_t bh = sdesc(sB + off), bl = sdesc(sBl + off);
+                        tc_mma<KIND>(d, ah, bh, idesc, (!hfirst || kk > 0) ? 1u : 0u);
+                        tc_mma<KIND>(d, ah, bl, idesc, 1u);
+                        tc_mma<KIND>(d, al, bh, idesc, 1u);
                     }
                     tc_commit(smem_u32(&bar_empty[stage]));
+                    if (hlast) {
+                        tc_commit(smem_u32(&bar_hfull[buf]));
+                        hblk++;
+                    }
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
-                if (!ok) break;
-                tc_commit(smem_u32(&bar_cfull));
-                local++;
             }
         }
     } else {
@@ -375,7 +366,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
         const int vc = p.dm.vc;
         const int nhb = (nch + p.kb - 1) / p.kb;
         const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
-        uint32_t hblk = 0, local = 0;
+        uint32_t hblk = 0;
         bool ok = true;
         for (int64_t it = blockIdx.x; it < p.nitems && ok; it += gridDim.x) {
             const Item w = decode(p, it);
@@ -387,8 +378,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
 #pragma unroll
             for (int j = 0; j < 128; j++) total[j] = 0.f;
             for (int hb = 0; hb < nhb; hb++) {
+                const uint32_t buf = hblk & 1u;
                 int good = 1;
-                if (lane == 0) good = mbar_wait(smem_u32(&bar_hfull), hblk & 1u, &abort_sh) ? 1 : 0;
+                if (lane == 0) good = mbar_wait(smem_u32(&bar_hfull[buf]), (hblk >> 1) & 1u, &abort_sh) ? 1 : 0;
                 good = __shfl_sync(0xffffffffu, good, 0);
                 __syncwarp();
                 if (!good) { ok = false; break; }
@@ -396,44 +388,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
 #pragma unroll
                 for (int c4 = 0; c4 < 4; c4++) {
                     uint32_t r[32];
-                    tc_ld32(tmem_h + lane_off + (uint32_t)(half * 128 + c4 * 32), r);
+                    tc_ld32(tmem + lane_off + buf * (uint32_t)BN + (uint32_t)(half * 128 + c4 * 32), r);
 #pragma unroll
                     for (int j = 0; j < 32; j++) total[c4 * 32 + j] += __uint_as_float(r[j]);
                 }
                 tc_fence_before();
-                mbar_arrive(smem_u32(&bar_hempty));
+                mbar_arrive(smem_u32(&bar_hempty[buf]));
                 hblk++;
             }
             if (!ok) {
                 if (lane == 0) fail(&abort_sh, p.err, DERR_TIMEOUT_TMEM);
                 break;
             }
-            int good = 1;
-            if (lane == 0) good = mbar_wait(smem_u32(&bar_cfull), local & 1u, &abort_sh) ? 1 : 0;
-            good = __shfl_sync(0xffffffffu, good, 0);
-            __syncwarp();
-            if (!good) {
-                if (lane == 0) fail(&abort_sh, p.err, DERR_TIMEOUT_TMEM);
-                break;
-            }
-            tc_fence_after();
-#pragma unroll
-            for (int c4 = 0; c4 < 4; c4++) {
-                uint32_t r[32];
-                tc_ld32(tmem_c + lane_off + (uint32_t)(half * 128 + c4 * 32), r);
-#pragma unroll
-                for (int j = 0; j < 32; j++) total[c4 * 32 + j] += __uint_as_float(r[j]);
-            }
-            tc_fence_before();
-            mbar_arrive(smem_u32(&bar_cempty));
-            local++;
+            // rows of 16 consecutive c per half warp: group 0 and 2 in their own
+            // [a][b][c] order, group 1 at [b][a][c] (aligned with W, see tcorr_internal.cuh)
             const int b = w.bt * PB + lb, c = w.ct * PC + lc;
             if (b < v && c < v) {
-                float *Ug = p.U + (int64_t)(w.tb * 3 + w.g) * v2 * vc + (int64_t)b * vc + c;
                 const int a0 = w.n * BN + half * 128;
+                const int64_t stride = w.g == 1 ? (int64_t)vc : (int64_t)v * vc;
+                const int64_t base = w.g == 1 ? (int64_t)b * v * vc + c : (int64_t)b * vc + c;
+                float *Ug = p.U + (int64_t)(w.tb * 3 + w.g) * v2 * vc + base + (int64_t)a0 * stride;
+                const int na = min(128, v - a0);
 #pragma unroll
                 for (int j = 0; j < 128; j++)
-                    if (a0 + j < v) Ug[(int64_t)(a0 + j) * v * vc] = total[j];
+                    if (j < na) Ug[(int64_t)j * stride] = total[j];
             }
         }
     }
@@ -567,7 +545,7 @@ cudaError_t launch_ugemm_tc(Handle *h, const GemmArgs &ga, cudaStream_t st) {
     const uint32_t fmt = tf ? 2u : 1u;
     p.idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BM >> 4) << 24);
     p.stage_tx = (uint32_t)(2 * A_BYTES + 2 * p.brows * ROW_BYTES);
-    p.kb = tf ? 1 : 2;  // two hi*hi instructions (TF32) / four (BF16) per H block
+    p.kb = 1;  // one chunk (2 K-steps x 3 products) per accumulator block
     const int grid = (int)std::min<int64_t>(h->sm_count, p.nitems);
     if (grid <= 0) return cudaSuccess;
     cudaError_t e;

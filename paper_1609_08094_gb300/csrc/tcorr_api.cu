@@ -383,7 +383,7 @@ tcorr_status tcorr_create(tcorr_t *out, int o, int v, const double *eps_occ,
         h.dm.dp = round_up(v, KPAD);
         h.dm.lp = round_up(o, KPAD);
         h.dm.vc = round_up(v, UPAD);
-        h.epi_te = h.prec == TCORR_FP64 ? 8 : 16;
+        h.epi_te = 8;
         const int64_t ntask = o64 * (o64 + 1) * (o64 + 2) / 6;
         h.u_task_bytes = (size_t)3 * v * v * h.dm.vc * (h.prec == TCORR_FP64 ? 8 : 4);
         size_t free_b = 0, total_b = 0;

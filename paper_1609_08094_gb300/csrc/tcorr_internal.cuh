@@ -46,6 +46,11 @@ struct Dims {
 //                      + sum_l AoN[q][s][a][l] T2K[p][b][c][l]
 //                      + sum_l AoN[p][s][a][l] T2K[q][c][b][l]
 // and W^{abc}_{ijk} = U^{i;j,k}[a][b][c] + U^{j;i,k}[b][a][c] + U^{k;i,j}[c][a][b].
+// Storage of the three group tensors in the U scratch ([ntb][3][v][v][vc]):
+//   FP64 path: each U^g in its own [a][b][c] order (read transposed by the
+//   FP64 epilogue);  mixed paths: slots 0 and 2 in their own [a][b][c] order,
+//   slot 1 transposed to [b][a][c], so that W[x][y][z] = S0[x][y][z] +
+//   S1[x][y][z] + S2[z][x][y] (S = stored slot).
 struct Operands {
     void *G = nullptr, *T2K = nullptr, *T2R = nullptr, *AoN = nullptr;       // FP64 or hi part
     void *Glo = nullptr, *T2Klo = nullptr, *T2Rlo = nullptr, *AoNlo = nullptr;  // lo part (mixed)
