@@ -317,29 +317,77 @@ __global__ void __launch_bounds__(NT) epilogue_f32_kernel(const EpiParams p) {
 
     const float base = base_s;
     float a4 = 0.f, a5 = 0.f;
-    for (int s = 0; s < 6; s++) {
-        if (!distinct[s]) continue;
-        const int p0 = pos[s][0], p1 = pos[s][1], p2 = pos[s][2];
-        // cube slots holding W at the five other orderings of this slot's indices
-        const float *W0 = Ws + comp[s][0] * FSLOT, *W1 = Ws + comp[s][1] * FSLOT;
-        const float *W2 = Ws + comp[s][2] * FSLOT, *W3 = Ws + comp[s][3] * FSLOT;
-        const float *W4 = Ws + comp[s][4] * FSLOT, *W5 = Ws + comp[s][5] * FSLOT;
+    if (ob[0] < ob[1] && ob[1] < ob[2]) {
+        // Distinct blocks: each thread takes element orbits, the six orderings
+        // of one (a,b,c) with a in A, b in B, c in C.  Slot q holds the element
+        // with indices ordered as q (slots 0..5 = abc, acb, bac, bca, cab, cba);
+        // even slots 0,3,4, odd slots 1,2,5.  With E and O the sums of W over
+        // the even and odd slots, Z at slot q is 6 w_q + 2E - 4O (q even) or
+        // 6 w_q + 2O - 4E (q odd), and all six share one denominator.
+        const int A0 = ob[0] * F8, B0 = ob[1] * F8, C0 = ob[2] * F8;
         for (int l = tid; l < 512; l += NT) {
-            const int l0 = l >> 6, l1 = (l >> 3) & 7, l2 = l & 7;
-            const int x = ob[p0] * F8 + l0, y = ob[p1] * F8 + l1, z = ob[p2] * F8 + l2;
-            if (x >= v || y >= v || z >= v) continue;
-            const float w0 = W0[l0 * FP0 + l1 * FP1 + l2];
-            // Z = 8 W(abc) - 4 (W(acb) + W(bac) + W(cba)) + 2 (W(bca) + W(cab))
-            const float zv = 8.f * w0 -
-                             4.f * (W1[l0 * FP0 + l2 * FP1 + l1] + W2[l1 * FP0 + l0 * FP1 + l2] +
-                                    W5[l2 * FP0 + l1 * FP1 + l0]) +
-                             2.f * (W3[l1 * FP0 + l2 * FP1 + l0] + W4[l2 * FP0 + l0 * FP1 + l1]);
-            const float yv = T1s[0][p0][l0] * OVs[0][p1][p2][l1 * F8 + l2] +
-                             T1s[1][p1][l1] * OVs[1][p0][p2][l0 * F8 + l2] +
-                             T1s[2][p2][l2] * OVs[2][p0][p1][l0 * F8 + l1];
-            const float r = __frcp_rn(base + (Dls[p0][l0] + Dls[p1][l1] + Dls[p2][l2]));
-            a4 = fmaf(zv * w0, r, a4);
-            a5 = fmaf(zv * yv, r, a5);
+            const int la = l >> 6, lb = (l >> 3) & 7, lc = l & 7;
+            if (A0 + la >= v || B0 + lb >= v || C0 + lc >= v) continue;
+            const float w0 = Ws[0 * FSLOT + la * FP0 + lb * FP1 + lc];
+            const float w1 = Ws[1 * FSLOT + la * FP0 + lc * FP1 + lb];
+            const float w2 = Ws[2 * FSLOT + lb * FP0 + la * FP1 + lc];
+            const float w3 = Ws[3 * FSLOT + lb * FP0 + lc * FP1 + la];
+            const float w4 = Ws[4 * FSLOT + lc * FP0 + la * FP1 + lb];
+            const float w5 = Ws[5 * FSLOT + lc * FP0 + lb * FP1 + la];
+            // t1 of occupied i, j, k at a, b, c
+            const float tia = T1s[0][0][la], tib = T1s[0][1][lb], tic = T1s[0][2][lc];
+            const float tja = T1s[1][0][la], tjb = T1s[1][1][lb], tjc = T1s[1][2][lc];
+            const float tka = T1s[2][0][la], tkb = T1s[2][1][lb], tkc = T1s[2][2][lc];
+            // (j u | k w), (i u | k w), (i u | j w) for ordered pairs of {a, b, c}
+#define OVV(sl, pu, pw, lu, lw) OVs[sl][pu][pw][(lu) * F8 + (lw)]
+            const float jk_bc = OVV(0, 1, 2, lb, lc), jk_cb = OVV(0, 2, 1, lc, lb), jk_ac = OVV(0, 0, 2, la, lc);
+            const float jk_ca = OVV(0, 2, 0, lc, la), jk_ab = OVV(0, 0, 1, la, lb), jk_ba = OVV(0, 1, 0, lb, la);
+            const float ik_bc = OVV(1, 1, 2, lb, lc), ik_cb = OVV(1, 2, 1, lc, lb), ik_ac = OVV(1, 0, 2, la, lc);
+            const float ik_ca = OVV(1, 2, 0, lc, la), ik_ab = OVV(1, 0, 1, la, lb), ik_ba = OVV(1, 1, 0, lb, la);
+            const float ij_bc = OVV(2, 1, 2, lb, lc), ij_cb = OVV(2, 2, 1, lc, lb), ij_ac = OVV(2, 0, 2, la, lc);
+            const float ij_ca = OVV(2, 2, 0, lc, la), ij_ab = OVV(2, 0, 1, la, lb), ij_ba = OVV(2, 1, 0, lb, la);
+#undef OVV
+            // Y at each ordering q of (a,b,c): t^{q0}_i (j q1|k q2) + t^{q1}_j (i q0|k q2) + t^{q2}_k (i q0|j q1)
+            const float y0 = tia * jk_bc + tjb * ik_ac + tkc * ij_ab;
+            const float y1 = tia * jk_cb + tjc * ik_ab + tkb * ij_ac;
+            const float y2 = tib * jk_ac + tja * ik_bc + tkc * ij_ba;
+            const float y3 = tib * jk_ca + tjc * ik_ba + tka * ij_bc;
+            const float y4 = tic * jk_ab + tja * ik_cb + tkb * ij_ca;
+            const float y5 = tic * jk_ba + tjb * ik_ca + tka * ij_cb;
+            const float E = w0 + w3 + w4, O = w1 + w2 + w5;
+            const float ww = w0 * w0 + w1 * w1 + w2 * w2 + w3 * w3 + w4 * w4 + w5 * w5;
+            const float wy = w0 * y0 + w1 * y1 + w2 * y2 + w3 * y3 + w4 * y4 + w5 * y5;
+            const float s4 = 6.f * ww + 2.f * (E * E + O * O) - 8.f * E * O;
+            const float s5 = 6.f * wy + (2.f * E - 4.f * O) * (y0 + y3 + y4) + (2.f * O - 4.f * E) * (y1 + y2 + y5);
+            const float r = __fdividef(1.f, base + (Dls[0][la] + Dls[1][lb] + Dls[2][lc]));
+            a4 = fmaf(s4, r, a4);
+            a5 = fmaf(s5, r, a5);
+        }
+    } else {
+        // blocks repeat: element by element over the distinct cube slots
+        for (int s = 0; s < 6; s++) {
+            if (!distinct[s]) continue;
+            const int p0 = pos[s][0], p1 = pos[s][1], p2 = pos[s][2];
+            const float *W0 = Ws + comp[s][0] * FSLOT, *W1 = Ws + comp[s][1] * FSLOT;
+            const float *W2 = Ws + comp[s][2] * FSLOT, *W3 = Ws + comp[s][3] * FSLOT;
+            const float *W4 = Ws + comp[s][4] * FSLOT, *W5 = Ws + comp[s][5] * FSLOT;
+            for (int l = tid; l < 512; l += NT) {
+                const int l0 = l >> 6, l1 = (l >> 3) & 7, l2 = l & 7;
+                const int x = ob[p0] * F8 + l0, y = ob[p1] * F8 + l1, z = ob[p2] * F8 + l2;
+                if (x >= v || y >= v || z >= v) continue;
+                const float w0 = W0[l0 * FP0 + l1 * FP1 + l2];
+                // Z = 8 W(abc) - 4 (W(acb) + W(bac) + W(cba)) + 2 (W(bca) + W(cab))
+                const float zv = 8.f * w0 -
+                                 4.f * (W1[l0 * FP0 + l2 * FP1 + l1] + W2[l1 * FP0 + l0 * FP1 + l2] +
+                                        W5[l2 * FP0 + l1 * FP1 + l0]) +
+                                 2.f * (W3[l1 * FP0 + l2 * FP1 + l0] + W4[l2 * FP0 + l0 * FP1 + l1]);
+                const float yv = T1s[0][p0][l0] * OVs[0][p1][p2][l1 * F8 + l2] +
+                                 T1s[1][p1][l1] * OVs[1][p0][p2][l0 * F8 + l2] +
+                                 T1s[2][p2][l2] * OVs[2][p0][p1][l0 * F8 + l1];
+                const float r = __fdividef(1.f, base + (Dls[p0][l0] + Dls[p1][l1] + Dls[p2][l2]));
+                a4 = fmaf(zv * w0, r, a4);
+                a5 = fmaf(zv * yv, r, a5);
+            }
         }
     }
     for (int off = 16; off > 0; off >>= 1) {
