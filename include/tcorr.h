@@ -60,7 +60,10 @@ typedef struct {
                            1: they are host pointers (pageable or pinned), copied in */
     int batch_tasks;    /* tasks per internal batch, 0 = chosen from the scratch budget */
     int profile;        /* 1: time every kernel class with CUDA events (tcorr_kernel_times) */
-    int reserved[4];    /* must be zero */
+    int test_stall;     /* testing only, 0 in normal use: 1 makes the tensor-core kernel withhold
+                           one chunk's loads so that a bounded device-side wait expires; the
+                           energy call then returns TCORR_ETIMEOUT and the context stays usable */
+    int reserved[3];    /* must be zero */
 } tcorr_opts;           /* zero-initialised = defaults */
 
 /*

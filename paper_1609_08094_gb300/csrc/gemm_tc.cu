@@ -58,7 +58,9 @@ constexpr int A_BYTES = BM * ROW_BYTES; // 8 KB
 constexpr int B_BYTES = BN * ROW_BYTES; // 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s per wait
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s of wall time per wait ...
+constexpr uint32_t WAIT_MIN_POLLS = 1u << 18;      // ... and at least this many polls, so that time
+                                                   // spent off the GPU (pre-emption) never counts
 
 enum { MAP_G_NAT = 0, MAP_G_SWP, MAP_T2K_NAT, MAP_T2K_SWP, MAP_T2R, MAP_AON, NMAP };
 
@@ -73,7 +75,8 @@ struct TcParams {
     int64_t nitems;
     uint32_t idesc_base;
     uint32_t stage_tx;
-    int kb;  // K chunks per H block
+    int kb;            // K chunks per accumulator block
+    int inject_stall;  // testing only: CTA 0 withholds the loads of its first chunk
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -105,8 +108,8 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait on one mbarrier phase; false on expiry or when another role
-// has already aborted.
+// Bounded wait on one mbarrier phase; false on expiry (both the wall-time
+// and the poll limit passed) or when another role has already aborted.
 __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
     if (mbar_test(bar, parity)) return true;
     const uint64_t t0 = gtimer();
@@ -114,7 +117,7 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
         if (mbar_test(bar, parity)) return true;
         if ((it & 63) == 0) {
             if (*abort_flag) return false;
-            if (gtimer() - t0 > WAIT_LIMIT_NS) return false;
+            if (it >= WAIT_MIN_POLLS && gtimer() - t0 > WAIT_LIMIT_NS) return false;
         }
     }
 }
@@ -257,6 +260,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
             int last_phase[STAGES];
             for (int s = 0; s < STAGES; s++) last_phase[s] = -1;
             bool ok = true;
+            bool inject = p.inject_stall != 0 && blockIdx.x == 0;
             for (int64_t it = blockIdx.x; it < p.nitems && ok; it += gridDim.x) {
                 const Item w = decode(p, it);
                 int s, pp, q;
@@ -288,10 +292,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                         case 2: amap = MAP_T2K_NAT; aslice = pp; bmap = MAP_AON; brow = q * o + s; break;
                         default: amap = MAP_T2K_SWP; aslice = q; bmap = MAP_AON; brow = pp * o + s; break;
                     }
-                    tma_load_4d(sA, &p.map[amap][0], full, k0, cc, cb, aslice);
-                    tma_load_4d(sAl, &p.map[amap][1], full, k0, cc, cb, aslice);
-                    tma_load_3d(sB, &p.map[bmap][0], full, k0, ca, brow);
-                    tma_load_3d(sBl, &p.map[bmap][1], full, k0, ca, brow);
+                    if (inject) {
+                        inject = false;
+                        last_phase[stage] = -1;  // nothing in flight: the consumer's wait must expire
+                    } else {
+                        tma_load_4d(sA, &p.map[amap][0], full, k0, cc, cb, aslice);
+                        tma_load_4d(sAl, &p.map[amap][1], full, k0, cc, cb, aslice);
+                        tma_load_3d(sB, &p.map[bmap][0], full, k0, ca, brow);
+                        tma_load_3d(sBl, &p.map[bmap][1], full, k0, ca, brow);
+                    }
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
             }
@@ -546,6 +555,7 @@ cudaError_t launch_ugemm_tc(Handle *h, const GemmArgs &ga, cudaStream_t st) {
     p.idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BM >> 4) << 24);
     p.stage_tx = (uint32_t)(2 * A_BYTES + 2 * p.brows * ROW_BYTES);
     p.kb = 1;  // one chunk (2 K-steps x 3 products) per accumulator block
+    p.inject_stall = h->inject_stall;
     const int grid = (int)std::min<int64_t>(h->sm_count, p.nitems);
     if (grid <= 0) return cudaSuccess;
     cudaError_t e;

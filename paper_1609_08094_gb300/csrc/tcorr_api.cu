@@ -345,6 +345,10 @@ tcorr_status tcorr_create(tcorr_t *out, int o, int v, const double *eps_occ,
     }
     tcorr_opts op{};
     if (opts) op = *opts;
+    if (op.test_stall != 0 && op.test_stall != 1) {
+        g_create_error = "test_stall must be 0 or 1";
+        return TCORR_EINVAL;
+    }
     for (int r : op.reserved)
         if (r != 0) {
             g_create_error = "reserved option fields must be zero";
@@ -370,6 +374,7 @@ tcorr_status tcorr_create(tcorr_t *out, int o, int v, const double *eps_occ,
         h.stream = static_cast<cudaStream_t>(stream);
         h.prec = op.prec;
         h.profile = op.profile;
+        h.inject_stall = op.test_stall;
         int dev = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&h.sm_count, cudaDevAttrMultiProcessorCount, dev));

@@ -60,6 +60,7 @@ struct Handle {
     Dims dm{};
     int prec = TCORR_FP64;
     int profile = 0;
+    int inject_stall = 0;   // testing: make a tensor-core pipeline wait expire
     int batch = 1;          // tasks per batch
     int sm_count = 0, cc_major = 0, cc_minor = 0;
     cudaStream_t stream = nullptr;

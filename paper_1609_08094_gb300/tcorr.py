@@ -33,7 +33,7 @@ class TcorrError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("host_inputs", ctypes.c_int),
                 ("batch_tasks", ctypes.c_int), ("profile", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("test_stall", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 def library_path() -> str:
@@ -119,7 +119,7 @@ class Tcorr:
     None for torch's current stream (device inputs) / the default stream."""
 
     def __init__(self, o, v, eps_occ, eps_vir, t1, t2, vvvo, ooov, ovov, prec="fp64",
-                 batch_tasks=0, profile=False, stream=None):
+                 batch_tasks=0, profile=False, stream=None, test_stall=False):
         lib = load()
         arrays = dict(eps_occ=eps_occ, eps_vir=eps_vir, t1=t1, t2=t2, vvvo=vvvo, ooov=ooov,
                       ovov=ovov)
@@ -133,7 +133,8 @@ class Tcorr:
         if isinstance(prec, str):
             prec = PREC[prec.lower()]
         opts = Opts(prec=int(prec), host_inputs=0 if on_device else 1,
-                    batch_tasks=int(batch_tasks), profile=1 if profile else 0)
+                    batch_tasks=int(batch_tasks), profile=1 if profile else 0,
+                    test_stall=1 if test_stall else 0)
         if stream is None and on_device:
             import torch
             stream = torch.cuda.current_stream(t2.device)

@@ -72,3 +72,22 @@ def test_mixed_edge_cases(prec):
     inst.t1 = np.zeros_like(inst.t1)
     e4, e5, e = energy(inst, prec)
     assert e5 == 0.0 and e == e4
+
+
+def test_bounded_wait_expiry_reports_timeout_and_context_survives():
+    """Failure detection without a fault: the test-only option makes the
+    tensor-core producer of CTA 0 withhold one chunk's loads, so the MMA
+    issuer's bounded wait expires.  The call must return TCORR_ETIMEOUT (no
+    hang, no fault) and the next normal call on the same context must work."""
+    import time
+    inst = synth.make_instance(3, 40, None, 41)
+    dev = inst.to("cuda")
+    with tcorr.Tcorr.from_instance(dev, prec="tf32x3", test_stall=True) as t:
+        t0 = time.time()
+        with pytest.raises(tcorr.TcorrError) as exc:
+            t.energy()
+        assert exc.value.status == 4  # TCORR_ETIMEOUT
+        assert time.time() - t0 < 60
+    ref = oracle.energy(inst)
+    got = energy(inst, "tf32x3")
+    assert rel(got[2], ref[2]) <= MIXED_TOL
