@@ -28,7 +28,7 @@
 //             swizzled rows.
 //   warp 1  : allocates 512 TMEM columns; one thread issues tcgen05.mma
 //             (M = 128, N <= 256, 2 K-steps x 3 products per chunk) into the
-//             block accumulator of the current K block.
+//             accumulator of the current K block of KB = 2 chunks.
 //   warps 2-9: two warps per TMEM lane quarter, 128 columns each: drain each
 //             block into the register total, then store the U rows (rows of
 //             16 consecutive c, coalesced) at the end of the tile.
@@ -329,40 +329,59 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                 const int nvalid = min(BN, v - w.n * BN);
                 const int N = (nvalid + 15) / 16 * 16;
                 const uint32_t idesc = p.idesc_base | ((uint32_t)(N >> 3) << 17);
-                for (int ch = 0; ch < nch && ok; ch++) {
-                    if (!mbar_wait(smem_u32(&bar_full[stage]), phase, &abort_sh)) {
-                        fail(&abort_sh, p.err, DERR_TIMEOUT_FULL);
-                        ok = false;
-                        break;
-                    }
-                    const bool hfirst = (ch % p.kb) == 0;
-                    const bool hlast = ((ch + 1) % p.kb) == 0 || ch == nch - 1;
+                // K blocks of kb chunks: the small hi*lo and lo*hi products of each
+                // chunk are issued as its data lands, the dominant hi*hi products of
+                // the whole block last, so that the truncation of every instruction
+                // acts on the smallest possible accumulator; the block's stages are
+                // released together once its last MMA is issued.
+                for (int c0 = 0; c0 < nch && ok; c0 += p.kb) {
+                    const int nb = min(p.kb, nch - c0);
                     const uint32_t buf = hblk & 1u;
-                    if (hfirst &&
-                        !mbar_wait(smem_u32(&bar_hempty[buf]), ((hblk >> 1) & 1u) ^ 1u, &abort_sh)) {
-                        fail(&abort_sh, p.err, DERR_TIMEOUT_TMEM);
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t d = tmem + buf * (uint32_t)BN;
-                    const uint32_t sA = sbase + stage * STAGE_BYTES, sAl = sA + A_BYTES;
-                    const uint32_t sB = sAl + A_BYTES, sBl = sB + B_BYTES;
+                    int st0 = stage;
+                    for (int cb = 0; cb < nb; cb++) {
+                        if (!mbar_wait(smem_u32(&bar_full[stage]), phase, &abort_sh)) {
+                            fail(&abort_sh, p.err, DERR_TIMEOUT_FULL);
+                            ok = false;
+                            break;
+                        }
+                        if (cb == 0 &&
+                            !mbar_wait(smem_u32(&bar_hempty[buf]), ((hblk >> 1) & 1u) ^ 1u, &abort_sh)) {
+                            fail(&abort_sh, p.err, DERR_TIMEOUT_TMEM);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d = tmem + buf * (uint32_t)BN;
+                        const uint32_t sA = sbase + stage * STAGE_BYTES, sAl = sA + A_BYTES;
+                        const uint32_t sB = sAl + A_BYTES, sBl = sB + B_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < 2; kk++) {
-                        const uint32_t off = kk * 32;
-                        const uint64_t ah = sdesc(sA + off), al = sdesc(sAl + off);
-                        const uint64_t bh = sdesc(sB + off), bl = sdesc(sBl + off);
-                        tc_mma<KIND>(d, ah, bh, idesc, (!hfirst || kk > 0) ? 1u : 0u);
-                        tc_mma<KIND>(d, ah, bl, idesc, 1u);
-                        tc_mma<KIND>(d, al, bh, idesc, 1u);
+                        for (int kk = 0; kk < 2; kk++) {
+                            const uint32_t off = kk * 32;
+                            tc_mma<KIND>(d, sdesc(sA + off), sdesc(sBl + off), idesc,
+                                         (cb > 0 || kk > 0) ? 1u : 0u);
+                            tc_mma<KIND>(d, sdesc(sAl + off), sdesc(sB + off), idesc, 1u);
+                        }
+                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
-                    tc_commit(smem_u32(&bar_empty[stage]));
-                    if (hlast) {
-                        tc_commit(smem_u32(&bar_hfull[buf]));
-                        hblk++;
+                    if (!ok) break;
+                    const uint32_t d = tmem + buf * (uint32_t)BN;
+                    int sj = st0;
+                    for (int cb = 0; cb < nb; cb++) {
+                        const uint32_t sA = sbase + sj * STAGE_BYTES, sB = sA + 2 * A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < 2; kk++) {
+                            const uint32_t off = kk * 32;
+                            tc_mma<KIND>(d, sdesc(sA + off), sdesc(sB + off), idesc, 1u);
+                        }
+                        if (++sj == STAGES) sj = 0;
                     }
-                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    sj = st0;
+                    for (int cb = 0; cb < nb; cb++) {
+                        tc_commit(smem_u32(&bar_empty[sj]));
+                        if (++sj == STAGES) sj = 0;
+                    }
+                    tc_commit(smem_u32(&bar_hfull[buf]));
+                    hblk++;
                 }
             }
         }
@@ -554,7 +573,7 @@ cudaError_t launch_ugemm_tc(Handle *h, const GemmArgs &ga, cudaStream_t st) {
     const uint32_t fmt = tf ? 2u : 1u;
     p.idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BM >> 4) << 24);
     p.stage_tx = (uint32_t)(2 * A_BYTES + 2 * p.brows * ROW_BYTES);
-    p.kb = 1;  // one chunk (2 K-steps x 3 products) per accumulator block
+    p.kb = 2;  // chunks per accumulator block (at most STAGES - 1: a block holds its stages)
     p.inject_stall = h->inject_stall;
     const int grid = (int)std::min<int64_t>(h->sm_count, p.nitems);
     if (grid <= 0) return cudaSuccess;
