@@ -437,9 +437,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                 const int64_t base = w.g == 1 ? (int64_t)b * v * vc + c : (int64_t)b * vc + c;
                 float *Ug = p.U + (int64_t)(w.tb * 3 + w.g) * v2 * vc + base + (int64_t)a0 * stride;
                 const int na = min(128, v - a0);
+                if (na == 128) {
 #pragma unroll
-                for (int j = 0; j < 128; j++)
-                    if (j < na) Ug[(int64_t)j * stride] = total[j];
+                    for (int j = 0; j < 128; j++) {
+                        *Ug = total[j];
+                        Ug += stride;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 128; j++) {
+                        if (j < na) *Ug = total[j];
+                        Ug += stride;
+                    }
+                }
             }
         }
     }
