@@ -37,6 +37,10 @@ METRIC = "(T) TFLOP/s, triples/s: FP64 vs mixed at ≤1e-6 rel ΔE; serving p50/
 WORKLOAD = dict(o=50, v=450, naux=1500, seed=2)
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (152 SMs x 2070 MHz x 2 DFMA/clk x 2 flop)
 FP64_PROBE_TFLOPS = 1.20     # DFMA throughput probe on this machine's GB300
+# DRAM read+write bytes of one full-task launch of ugemm_f64_kernel at o=50,
+# v=450 from one ncu capture (profiles/ugemm_f64_kernel_o50_v450.md); valid
+# for this kernel version and workload only
+F64_GEMM_TRAFFIC_BYTES = {(50, 450): 5157372672 + 2182112768}
 
 
 def parse():
@@ -57,6 +61,23 @@ def parse():
     ap.add_argument("--naux", type=int, default=WORKLOAD["naux"])
     ap.add_argument("--seed", type=int, default=WORKLOAD["seed"])
     return ap.parse_args()
+
+
+def measured_peaks():
+    """Measured GB300 peaks written beside the repository (HBM GB/s, dense
+    BF16 TFLOP/s burst and sustained); the profiling recipe's fallback
+    figures when the file is absent."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16": d["bf16_tflops"],
+                "bf16_sustained": d["bf16_tflops_sustained"], "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
+
+
+# nominal dense tensor rates: TF32 1.1 PFLOP/s vs BF16 2.25 PFLOP/s
+TF32_PER_BF16 = 1.1 / 2.25
 
 
 def sorted_tasks(o):
@@ -196,11 +217,10 @@ def main():
     ntask = len(tasks)
     fl_task = 12.0 * v ** 3 * (v + o)
     K, W, C = args.steps, args.warmup, args.tasks_per_step
-    # rank r, step s: a contiguous batch of C tasks (weak scaling over ranks)
-    span = (W + K) * C
+    from paper_1609_08094_gb300 import partition
 
-    def first_of(s):
-        return ((rank * span + s * C) % max(1, ntask - C))
+    def first_of(s):  # rank's batch at step s: disjoint across ranks (weak scaling)
+        return partition.step_batch(ntask, rank, world, s, C)
 
     # ---- FP64, device-resident inputs -------------------------------------
     t = tcorr.Tcorr.from_instance(inst, prec="fp64", profile=True, stream=stream)
@@ -258,7 +278,7 @@ def main():
             Cm = args.mixed_tasks_per_step
 
             def first_m(s, Cm=Cm):
-                return ((rank * (W + K) * Cm + s * Cm) % max(1, ntask - Cm))
+                return partition.step_batch(ntask, rank, world, s, Cm)
             msm, resm, kt = time_steps(tm, tasks, first_m, Cm, W, K, world, stream)
             msm = dist_max(msm, world)
             workm = sum(work_tasks(tasks, first_m(W + s), Cm) for s in range(K))
@@ -276,6 +296,19 @@ def main():
             em8 = tm.energy_range(first_m(W), min(Cm, 8))
             tf.close()
             ent["rel_err_vs_fp64"] = abs(em8[2] - ef[2]) / abs(ef[2])
+            pk = measured_peaks()
+            peak = pk["bf16"] * (TF32_PER_BF16 if prec == "tf32x3" else 1.0)
+            if ent["gemm_tflops"]:
+                ent["roofline"] = {
+                    "bound": "tensor", "kernel": f"ugemm_tc_kernel ({prec})",
+                    "achieved": ent["gemm_tflops"], "peak": peak, "unit": "TFLOP/s",
+                    "frac": ent["gemm_tflops"] / peak, "traffic": None,
+                    "tensor_achieved": 3 * ent["gemm_tflops"],
+                    "tensor_frac": 3 * ent["gemm_tflops"] / peak,
+                    "note": ("achieved counts algorithmic flops (12 v^3 (v+o) per task); the "
+                             "tensor pipe executes 3 products per flop (hi*hi, hi*lo, lo*hi): "
+                             "tensor_achieved.  peak: BF16 dense burst of " + pk["source"]
+                             + (" peaks x the nominal TF32/BF16 ratio" if prec == "tf32x3" else " peaks"))}
             ent["speedup_vs_fp64"] = ent["value"] / value
             mixed[prec] = ent
             tm.close()
@@ -319,7 +352,8 @@ def main():
         "triples_per_s": triples_s,
         "roofline": {"bound": "alu", "kernel": "ugemm_f64_kernel", "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": None,
+                     "traffic": (F64_GEMM_TRAFFIC_BYTES.get((o, v)) if gemm_n == work else None),
+                     "traffic_unit": "bytes per launch (one task)",
                      "peak_note": "nominal FP64 (no FP64 figure in the measured peaks); "
                                   f"DFMA probe measured {FP64_PROBE_TFLOPS} TFLOP/s"},
         "kernel_ms_share": shares,

@@ -8,7 +8,8 @@
 // GB300's FP64 rate is far below its tensor rates, so this kernel is bound by
 // the FP64 pipe: a register-tiled DFMA GEMM (CTA tile 128 pairs x 32 a, 16
 // outputs per thread, K staged through shared memory in chunks of 8 with a
-// register prefetch of the next chunk).  Operand rows are K-contiguous, so
+// register prefetch of the next chunk).  CTAs are ordered a-tile fastest so
+// that each pair tile of the large operand comes from HBM once.  Operand rows are K-contiguous, so
 // the swapped pair order (c,b) of two segments only changes which rows are
 // read, never the coalescing.
 #include "tcorr_internal.cuh"
@@ -36,8 +37,11 @@ __global__ void __launch_bounds__(NT) ugemm_f64_kernel(const F64Params p) {
     const int o = p.dm.o, v = p.dm.v, dp = p.dm.dp, lp = p.dm.lp, vc = p.dm.vc;
     const int64_t v2 = (int64_t)v * v;
     const int tid = threadIdx.x;
-    const int64_t p0 = (int64_t)blockIdx.x * TP;
-    const int a0 = blockIdx.y * TA;
+    // a tiles fastest: the CTAs sharing one pair tile (the large A operand)
+    // run back to back, so it is read from HBM once and then hits L2
+    const int nat = (v + TA - 1) / TA;
+    const int64_t p0 = (int64_t)(blockIdx.x / nat) * TP;
+    const int a0 = (blockIdx.x % nat) * TA;
     const int tb = blockIdx.z / 3, g = blockIdx.z % 3;
     const int *tk = p.tasks + 3 * (p.task0 + tb);
     const int ti = tk[0], tj = tk[1], tkk = tk[2];
@@ -171,9 +175,9 @@ cudaError_t launch_ugemm_f64(const Operands &op, const GemmArgs &ga, cudaStream_
     p.task0 = ga.task0;
     p.U = static_cast<double *>(ga.U);
     const int64_t v2 = (int64_t)ga.dm.v * ga.dm.v;
-    dim3 grid((unsigned)((v2 + TP - 1) / TP), (unsigned)((ga.dm.v + TA - 1) / TA),
-              (unsigned)(3 * ga.ntb));
-    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+    const int64_t tiles = ((v2 + TP - 1) / TP) * ((ga.dm.v + TA - 1) / TA);
+    dim3 grid((unsigned)tiles, 1, (unsigned)(3 * ga.ntb));
+    if (tiles > 0x7fffffff || grid.z > 65535) return cudaErrorInvalidConfiguration;
     ugemm_f64_kernel<<<grid, NT, 0, st>>>(p);
     return cudaGetLastError();
 }
