@@ -58,12 +58,20 @@ typedef struct {
     int prec;           /* tcorr_precision; 0 = TCORR_FP64 */
     int host_inputs;    /* 0: the array arguments of tcorr_create are device pointers;
                            1: they are host pointers (pageable or pinned), copied in */
-    int batch_tasks;    /* tasks per internal batch, 0 = chosen from the scratch budget */
+    int batch_tasks;    /* tasks per internal batch (batch handle: at most this many tasks per
+                           wave), 0 = chosen from the scratch budget */
     int profile;        /* 1: time every kernel class with CUDA events (tcorr_kernel_times) */
     int test_stall;     /* testing only, 0 in normal use: 1 makes the tensor-core kernel withhold
                            one chunk's loads so that a bounded device-side wait expires; the
                            energy call then returns TCORR_ETIMEOUT and the context stays usable */
-    int reserved[3];    /* must be zero */
+    int tune;           /* tensor-core tile shape per problem shape: 0 = cost model (fewest padded
+                           tiles), 1 = measured at create time (each candidate timed on the
+                           problem's own operands; cached per (precision, o, v) in the process) */
+    int eager;          /* batch handle: 1 = launch the waves directly on every call instead of
+                           replaying the CUDA graph captured on the first call */
+    int wave_mb;        /* batch handle: U scratch per wave in MiB (0 = 96, sized so that one
+                           wave's U stays in L2 between the contraction and the epilogue);
+                           raised to one task of the largest problem when smaller */
 } tcorr_opts;           /* zero-initialised = defaults */
 
 /*
@@ -83,7 +91,7 @@ typedef struct {
  * once tcorr_create returns.  opts may be NULL (defaults).  stream is a
  * cudaStream_t or NULL.  On success *out receives the handle; on failure
  * *out is set to NULL and nothing is leaked.
- * Errors: EINVAL (NULL pointer, o < 1, v < 1, nonzero reserved field,
+ * Errors: EINVAL (NULL pointer, o < 1, v < 1, an option outside its range,
  * unknown precision), ENOMEM (footprint above free device memory),
  * EUNSUPPORTED (mixed precision on a device other than sm_103),
  * ECUDA.
@@ -145,6 +153,60 @@ const char *tcorr_status_string(tcorr_status s);
 int tcorr_version(void);
 
 /*
+ * Batch of independent problems ("molecules" of uneven o, v) evaluated
+ * together: the flattening of the per-problem task loops of Sec. 3 one level
+ * further, across problems.  All problems share one precision, one stream and
+ * one scratch; their tasks are cut into waves that fill the scratch, and each
+ * wave runs the same three launches as a single handle (persistent W
+ * contraction over the wave's (problem, task, group, tile) units, fused
+ * epilogue, per-task reduction), followed by one per-problem Kahan sum.  The
+ * launch sequence of a whole energy call is captured once into a CUDA graph
+ * (on the first call) and every call replays it (opts.eager = 1: launch the
+ * kernels directly instead; opts.profile and opts.test_stall imply it).  Tile
+ * shapes of the tensor-core contraction are chosen per problem shape
+ * (opts.tune).  Results do not depend on the other problems of the batch, on
+ * the wave cut or on graph replay: each problem's energies are bit-identical
+ * to those of a single handle with the same precision and tile shape.
+ */
+typedef struct tcorr_batch_s *tcorr_batch_t;
+
+typedef struct {
+    int o, v;           /* orbitals of this problem */
+    const double *eps_occ, *eps_vir, *t1, *t2, *vvvo, *ooov, *ovov;  /* as for tcorr_create */
+} tcorr_problem;
+
+/*
+ * Create a batch of n >= 1 problems.  problems[n] describes each as the
+ * arguments of tcorr_create do (device or host pointers per opts.host_inputs,
+ * read only during the call).  opts as for tcorr_create plus eager, wave_mb;
+ * opts.batch_tasks caps the tasks per wave.  Errors as for tcorr_create; the
+ * message of a failure is in tcorr_last_error(NULL).
+ */
+tcorr_status tcorr_batch_create(tcorr_batch_t *out, int n, const tcorr_problem *problems,
+                                const tcorr_opts *opts, void *stream);
+
+/* Number of problems in the batch (-1 for NULL). */
+int tcorr_batch_size(tcorr_batch_t b);
+
+/* Energies of every problem: e_out (host, [n][3] doubles) receives E[4], E[5],
+ * E(T) of each.  Synchronous on the batch's stream. */
+tcorr_status tcorr_batch_energy(tcorr_batch_t b, double *e_out);
+
+/* Tensor-core tile of problem idx: tile[0] = b values per pair tile (pb, with
+ * 128/pb values of c), tile[1] = K chunks per accumulator block.  {0, 0} for
+ * FP64 batches.  EINVAL if idx is out of range. */
+tcorr_status tcorr_batch_tile(tcorr_batch_t b, int idx, int *tile);
+
+/* Waves per energy call and the number of kernel launches they make. */
+tcorr_status tcorr_batch_plan(tcorr_batch_t b, int64_t *waves, int64_t *launches);
+
+/* As tcorr_kernel_times / tcorr_device_bytes / tcorr_last_error / tcorr_destroy. */
+tcorr_status tcorr_batch_kernel_times(tcorr_batch_t b, double *ms, int64_t *launches, int reset);
+int64_t tcorr_batch_device_bytes(tcorr_batch_t b);
+const char *tcorr_batch_last_error(tcorr_batch_t b);
+tcorr_status tcorr_batch_destroy(tcorr_batch_t b);
+
+/*
  * Allocation-free variant (the paper has no counterpart; it exists for
  * callers that must not allocate device memory: applications whose device
  * memory is owned entirely by their own pool or budget, and latency-sensitive
@@ -170,7 +232,7 @@ int tcorr_version(void);
  *    serialise them.
  */
 #define TCORR_NOALLOC_MAX_V 64
-#define TCORR_NOALLOC_SCRATCH_BYTES 6295552
+#define TCORR_NOALLOC_SCRATCH_BYTES 6299648
 tcorr_status tcorr_task_energy_noalloc(int o, int v, const double *eps_occ,
                                        const double *eps_vir, const double *t1,
                                        const double *t2, const double *vvvo,

@@ -33,23 +33,9 @@ __device__ __forceinline__ void kahan_add(double &s, double &c, double x) {
     s = t;
 }
 
-struct EpiParams {
-    Dims dm;
-    const int *tasks;
-    int64_t task0;
-    const void *U;
-    const double *eps_o, *eps_v;
-    const void *t1, *ovov;
-    const float *dev_f;
-    const int *orbits;
-    int norb;
-    double *partials;
-};
-
-// UT: storage type of U; CT: element arithmetic (double for the FP64
-// precision, float for the mixed precisions); TE: cube edge.
+// FP64 epilogue (the generic per-element form); TE: cube edge.
 template <typename UT, typename CT, int TE>
-__global__ void __launch_bounds__(NT) epilogue_kernel(const EpiParams p) {
+__global__ void __launch_bounds__(NT) epilogue_kernel(const Wave wv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *Ws = reinterpret_cast<CT *>(smem_raw);
     constexpr int TP = TE + 1;               // padded innermost extent
@@ -60,12 +46,15 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const EpiParams p) {
     __shared__ int distinct[6];
     __shared__ double red[NT / 32][2];
 
+    const int64_t item = blockIdx.x;
+    const Seg sg = wv.segs[seg_find(wv.segs, wv.nseg, item, [](const Seg &x) { return x.epi0; })];
+    const InstDesc &p = wv.descs[sg.inst];
     const int o = p.dm.o, v = p.dm.v, vc = p.dm.vc;
     const int64_t v2 = (int64_t)v * v;
-    const int orb = blockIdx.x, tb = blockIdx.y;
-    const int *tk = p.tasks + 3 * (p.task0 + tb);
+    const int tb = (int)((item - sg.epi0) / p.norb), orb = (int)((item - sg.epi0) % p.norb);
+    const int *tk = p.tasks + 3 * (sg.task0 + tb);
     const int ti = tk[0], tj = tk[1], tkk = tk[2];
-    double *out = p.partials + ((int64_t)tb * p.norb + orb) * 2;
+    double *out = wv.partials + sg.part_off + ((int64_t)tb * p.norb + orb) * 2;
     if (ti == tj && tj == tkk) {  // Z = 0 identically
         if (threadIdx.x == 0) { out[0] = 0.0; out[1] = 0.0; }
         return;
@@ -94,7 +83,7 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const EpiParams p) {
         distinct[tid] = d;
     }
 
-    const UT *U0 = static_cast<const UT *>(p.U) + (int64_t)(tb * 3 + 0) * v2 * vc;
+    const UT *U0 = static_cast<const UT *>(wv.U) + sg.u_off + (int64_t)(tb * 3 + 0) * v2 * vc;
     const UT *U1 = U0 + v2 * vc;
     const UT *U2 = U1 + v2 * vc;
 
@@ -134,10 +123,6 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const EpiParams p) {
         if (!distinct[s]) continue;
         CT a4 = CT(0), a5 = CT(0);
         const int X0 = blk[s][0] * TE, Y0 = blk[s][1] * TE, Z0 = blk[s][2] * TE;
-        CT base = CT(0);
-        if constexpr (sizeof(CT) == 4)
-            base = CT(eijk - p.eps_v[X0 < v ? X0 : 0] - p.eps_v[Y0 < v ? Y0 : 0] -
-                      p.eps_v[Z0 < v ? Z0 : 0]);
         for (int l = tid; l < NE; l += NT) {
             const int lv[3] = {l / (TE * TE), (l / TE) % TE, l % TE};
             const int x = X0 + lv[0], y = Y0 + lv[1], z = Z0 + lv[2];
@@ -152,11 +137,7 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const EpiParams p) {
             const CT w0 = Ws[s * CUBE + (lv[0] * TE + lv[1]) * TP + lv[2]];
             const CT yv = t1[ti * v + x] * ov_jk[y * ovs + z] + t1[tj * v + y] * ov_ik[x * ovs + z] +
                           t1[tkk * v + z] * ov_ij[x * ovs + y];
-            CT dn;
-            if constexpr (sizeof(CT) == 4)
-                dn = base + (p.dev_f[x] + p.dev_f[y] + p.dev_f[z]);
-            else
-                dn = eijk - p.eps_v[x] - p.eps_v[y] - p.eps_v[z];
+            const CT dn = eijk - p.eps_v[x] - p.eps_v[y] - p.eps_v[z];
             const CT r = CT(1) / dn;
             a4 += zv * w0 * r;
             a5 += zv * yv * r;
@@ -193,7 +174,7 @@ constexpr int F8 = 8;
 constexpr int FP0 = 69, FP1 = 8;    // plane / row pitch of a cube: at most 2-way bank conflicts
 constexpr int FSLOT = F8 * FP0;     // floats per cube slot
 
-__global__ void __launch_bounds__(NT) epilogue_f32_kernel(const EpiParams p) {
+__global__ void __launch_bounds__(NT) epilogue_f32_kernel(const Wave wv) {
     __shared__ float Ws[6 * FSLOT];
     __shared__ float T1s[3][3][F8];          // [occupied i,j,k][orbit block][local]
     __shared__ float OVs[3][3][3][F8 * F8];  // [(jk),(ik),(ij)][block][block][8x8]
@@ -205,12 +186,16 @@ __global__ void __launch_bounds__(NT) epilogue_f32_kernel(const EpiParams p) {
     __shared__ int ob[3];
     __shared__ double red[NT / 32][2];
 
+    const int64_t item = blockIdx.x;
+    const Seg sg = wv.segs[seg_find(wv.segs, wv.nseg, item, [](const Seg &x) { return x.epi0; })];
+    const InstDesc &p = wv.descs[sg.inst];
     const int o = p.dm.o, v = p.dm.v, vc = p.dm.vc;
     const int64_t v2 = (int64_t)v * v;
-    const int orb = blockIdx.x, tb = blockIdx.y, tid = threadIdx.x;
-    const int *tk = p.tasks + 3 * (p.task0 + tb);
+    const int tb = (int)((item - sg.epi0) / p.norb), orb = (int)((item - sg.epi0) % p.norb);
+    const int tid = threadIdx.x;
+    const int *tk = p.tasks + 3 * (sg.task0 + tb);
     const int ti = tk[0], tj = tk[1], tkk = tk[2];
-    double *out = p.partials + ((int64_t)tb * p.norb + orb) * 2;
+    double *out = wv.partials + sg.part_off + ((int64_t)tb * p.norb + orb) * 2;
     if (ti == tj && tj == tkk) {
         if (tid == 0) { out[0] = 0.0; out[1] = 0.0; }
         return;
@@ -269,7 +254,7 @@ __global__ void __launch_bounds__(NT) epilogue_f32_kernel(const EpiParams p) {
     // W[x][y][z] = S0[x][y][z] + S1[x][y][z] + S2[z][x][y]: slots 0 and 1 read
     // along z, slot 2 along y (all rows contiguous); all float4 loads of a
     // thread are issued before any use.
-    const float *S0 = static_cast<const float *>(p.U) + (int64_t)(tb * 3 + 0) * v2 * vc;
+    const float *S0 = static_cast<const float *>(wv.U) + sg.u_off + (int64_t)(tb * 3 + 0) * v2 * vc;
     const int64_t gs = v2 * vc;
     float4 ra[3], rb[3], rc[3];
 #pragma unroll
@@ -404,12 +389,16 @@ __global__ void __launch_bounds__(NT) epilogue_f32_kernel(const EpiParams p) {
     }
 }
 
-// One CTA per task of the batch: Kahan sum of the orbit partials, times m/6.
-__global__ void __launch_bounds__(NT) task_reduce_kernel(const int *tasks, int64_t task0, int norb,
-                                                         const double *partials, double *task_e) {
+// One CTA per task of the wave: Kahan sum of its orbit partials, times m/6.
+__global__ void __launch_bounds__(NT) task_reduce_kernel(const Wave wv) {
     __shared__ double red[NT][2];
-    const int tb = blockIdx.x, tid = threadIdx.x;
-    const double *pp = partials + (int64_t)tb * norb * 2;
+    const int64_t t = blockIdx.x;
+    const int tid = threadIdx.x;
+    const Seg sg = wv.segs[seg_find(wv.segs, wv.nseg, t, [](const Seg &x) { return x.red0; })];
+    const InstDesc &d = wv.descs[sg.inst];
+    const int tb = (int)(t - sg.red0);
+    const int norb = d.norb;
+    const double *pp = wv.partials + sg.part_off + (int64_t)tb * norb * 2;
     double s4 = 0.0, c4 = 0.0, s5 = 0.0, c5 = 0.0;
     for (int n = tid; n < norb; n += NT) { kahan_add(s4, c4, pp[2 * n]); kahan_add(s5, c5, pp[2 * n + 1]); }
     red[tid][0] = s4 - c4;
@@ -420,23 +409,24 @@ __global__ void __launch_bounds__(NT) task_reduce_kernel(const int *tasks, int64
         __syncthreads();
     }
     if (tid == 0) {
-        const int *tk = tasks + 3 * (task0 + tb);
+        const int *tk = d.tasks + 3 * (sg.task0 + tb);
         const int i = tk[0], j = tk[1], k = tk[2];
         const double m = (i == j && j == k) ? 0.0 : ((i == j || j == k) ? 3.0 : 6.0);
-        task_e[2 * (task0 + tb)] = red[0][0] * (m / 6.0);
-        task_e[2 * (task0 + tb) + 1] = red[0][1] * (m / 6.0);
+        d.task_e[2 * (sg.task0 + tb)] = red[0][0] * (m / 6.0);
+        d.task_e[2 * (sg.task0 + tb) + 1] = red[0][1] * (m / 6.0);
     }
 }
 
-// Single CTA: Kahan sum of task energies first..first+count-1 -> (E4, E5, E).
-__global__ void __launch_bounds__(NT) range_sum_kernel(const double *task_e, int64_t first,
-                                                       int64_t count, double *sums) {
+// One CTA per span: Kahan sum of task energies first..first+count-1 of the
+// span's problem -> (E4, E5, E).
+__global__ void __launch_bounds__(NT) span_sum_kernel(const SumSpan *spans) {
     __shared__ double red[NT][2];
+    const SumSpan sp = spans[blockIdx.x];
     const int tid = threadIdx.x;
     double s4 = 0.0, c4 = 0.0, s5 = 0.0, c5 = 0.0;
-    for (int64_t n = tid; n < count; n += NT) {
-        kahan_add(s4, c4, task_e[2 * (first + n)]);
-        kahan_add(s5, c5, task_e[2 * (first + n) + 1]);
+    for (int64_t n = tid; n < sp.count; n += NT) {
+        kahan_add(s4, c4, sp.task_e[2 * (sp.first + n)]);
+        kahan_add(s5, c5, sp.task_e[2 * (sp.first + n) + 1]);
     }
     red[tid][0] = s4 - c4;
     red[tid][1] = s5 - c5;
@@ -446,60 +436,40 @@ __global__ void __launch_bounds__(NT) range_sum_kernel(const double *task_e, int
         __syncthreads();
     }
     if (tid == 0) {
-        sums[0] = red[0][0];
-        sums[1] = red[0][1];
-        sums[2] = red[0][0] + red[0][1];
+        sp.out[0] = red[0][0];
+        sp.out[1] = red[0][1];
+        sp.out[2] = red[0][0] + red[0][1];
     }
-}
-
-template <typename UT, typename CT, int TE>
-cudaError_t launch_epi_t(const EpiParams &p, int ntb, cudaStream_t st) {
-    const size_t smem = sizeof(CT) * 6 * TE * TE * (TE + 1);
-    auto kern = epilogue_kernel<UT, CT, TE>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    dim3 grid((unsigned)p.norb, (unsigned)ntb);
-    kern<<<grid, NT, smem, st>>>(p);
-    return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_epilogue(int prec, const EpiArgs &ea, cudaStream_t st) {
-    EpiParams p;
-    p.dm = ea.dm;
-    p.tasks = ea.tasks;
-    p.task0 = ea.task0;
-    p.U = ea.U;
-    p.eps_o = ea.eps_o;
-    p.eps_v = ea.eps_v;
-    p.t1 = ea.t1;
-    p.ovov = ea.ovov;
-    p.dev_f = ea.dev_f;
-    p.orbits = ea.orbits;
-    p.norb = ea.norb;
-    p.partials = ea.partials;
-    if (ea.ntb > 65535) return cudaErrorInvalidConfiguration;
+int epilogue_orbits(int v) {
+    const int nb = (v + 7) / 8;
+    return nb * (nb + 1) * (nb + 2) / 6;
+}
+
+cudaError_t launch_epilogue(int prec, const Wave &w, cudaStream_t st) {
+    if (w.n_epi <= 0) return cudaSuccess;
+    if (w.n_epi > 0x7fffffff) return cudaErrorInvalidConfiguration;
     if (prec == TCORR_FP64) {
-        if (ea.te != 8) return cudaErrorInvalidValue;
-        return launch_epi_t<double, double, 8>(p, ea.ntb, st);
+        const size_t smem = sizeof(double) * 6 * 8 * 8 * 9;
+        epilogue_kernel<double, double, 8><<<(unsigned)w.n_epi, NT, smem, st>>>(w);
+    } else {
+        epilogue_f32_kernel<<<(unsigned)w.n_epi, NT, 0, st>>>(w);
     }
-    if (ea.te != F8) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)p.norb, (unsigned)ea.ntb);
-    epilogue_f32_kernel<<<grid, NT, 0, st>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_task_reduce(const EpiArgs &ea, cudaStream_t st) {
-    task_reduce_kernel<<<ea.ntb, NT, 0, st>>>(ea.tasks, ea.task0, ea.norb, ea.partials, ea.task_e);
+cudaError_t launch_task_reduce(const Wave &w, cudaStream_t st) {
+    if (w.n_red <= 0) return cudaSuccess;
+    task_reduce_kernel<<<(unsigned)w.n_red, NT, 0, st>>>(w);
     return cudaGetLastError();
 }
 
-cudaError_t launch_range_sum(const double *task_e, int64_t first, int64_t count, double *sums,
-                             cudaStream_t st) {
-    range_sum_kernel<<<1, NT, 0, st>>>(task_e, first, count, sums);
+cudaError_t launch_span_sums(const SumSpan *spans, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    span_sum_kernel<<<n, NT, 0, st>>>(spans);
     return cudaGetLastError();
 }
 

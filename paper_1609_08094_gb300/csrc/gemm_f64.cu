@@ -8,8 +8,8 @@
 // GB300's FP64 rate is far below its tensor rates, so this kernel is bound by
 // the FP64 pipe: a register-tiled DFMA GEMM (CTA tile 128 pairs x 32 a, 16
 // outputs per thread, K staged through shared memory in chunks of 8 with a
-// register prefetch of the next chunk).  CTAs are ordered a-tile fastest so
-// that each pair tile of the large operand comes from HBM once.  Operand rows are K-contiguous, so
+// register prefetch of the next chunk).  One flattened grid covers the work
+// units of every segment of a wave (one or many problems).  Operand rows are K-contiguous, so
 // the swapped pair order (c,b) of two segments only changes which rows are
 // read, never the coalescing.
 #include "tcorr_internal.cuh"
@@ -22,34 +22,39 @@ constexpr int TA = 32;   // a values per CTA tile
 constexpr int KC = 8;    // K chunk
 constexpr int NT = 256;  // threads
 
-struct F64Params {
-    Dims dm;
-    const double *G, *T2K, *T2R, *AoN;
-    const int *tasks;
-    int64_t task0;
-    double *U;
-};
-
-__global__ void __launch_bounds__(NT) ugemm_f64_kernel(const F64Params p) {
+__global__ void __launch_bounds__(NT) ugemm_f64_kernel(const Wave w) {
     __shared__ __align__(16) double As[KC][TP + 4];
     __shared__ __align__(16) double Bs[KC][TA + 4];
 
-    const int o = p.dm.o, v = p.dm.v, dp = p.dm.dp, lp = p.dm.lp, vc = p.dm.vc;
+    // work unit -> segment -> (task, group, pair tile, a tile); a tiles fastest,
+    // so the CTAs sharing one pair tile (the large A operand) run back to back
+    // and it is read from HBM once, then from L2
+    const int64_t unit = blockIdx.x;
+    const Seg sg = w.segs[seg_find(w.segs, w.nseg, unit, [](const Seg &x) { return x.gemm0; })];
+    const InstDesc &d = w.descs[sg.inst];
+    const int o = d.dm.o, v = d.dm.v, dp = d.dm.dp, lp = d.dm.lp, vc = d.dm.vc;
     const int64_t v2 = (int64_t)v * v;
-    const int tid = threadIdx.x;
-    // a tiles fastest: the CTAs sharing one pair tile (the large A operand)
-    // run back to back, so it is read from HBM once and then hits L2
     const int nat = (v + TA - 1) / TA;
-    const int64_t p0 = (int64_t)(blockIdx.x / nat) * TP;
-    const int a0 = (blockIdx.x % nat) * TA;
-    const int tb = blockIdx.z / 3, g = blockIdx.z % 3;
-    const int *tk = p.tasks + 3 * (p.task0 + tb);
+    const int64_t per_g = ((v2 + TP - 1) / TP) * nat;
+    int64_t local = unit - sg.gemm0;
+    const int tb = (int)(local / (3 * per_g));
+    local -= (int64_t)tb * 3 * per_g;
+    const int g = (int)(local / per_g);
+    const int64_t tile = local % per_g;
+    const int64_t p0 = (tile / nat) * TP;
+    const int a0 = (int)(tile % nat) * TA;
+    const int tid = threadIdx.x;
+    const int *tk = d.tasks + 3 * (sg.task0 + tb);
     const int ti = tk[0], tj = tk[1], tkk = tk[2];
     if (ti == tj && tj == tkk) return;  // i = j = k: zero energy, U never read
     int s, pp, q;
     if (g == 0) { s = ti; pp = tj; q = tkk; }
     else if (g == 1) { s = tj; pp = ti; q = tkk; }
     else { s = tkk; pp = ti; q = tj; }
+    const double *Gm = static_cast<const double *>(d.G);
+    const double *T2K = static_cast<const double *>(d.T2K);
+    const double *T2R = static_cast<const double *>(d.T2R);
+    const double *AoN = static_cast<const double *>(d.AoN);
 
     // A-row loader: row = tid>>1, half = tid&1 (4 doubles each)
     const int arow = tid >> 1, ahalf = tid & 1;
@@ -74,20 +79,20 @@ __global__ void __launch_bounds__(NT) ugemm_f64_kernel(const F64Params p) {
         else { seg = 3; kk = (chunk - 2 * nchunk_v - nchunk_o) * KC; }
         switch (seg) {
             case 0:
-                aptr = p.G + ((int64_t)q * v2 + row_nat) * dp + kk;
-                bptr = p.T2R + (((int64_t)s * o + pp) * v + ba) * dp + kk;
+                aptr = Gm + ((int64_t)q * v2 + row_nat) * dp + kk;
+                bptr = T2R + (((int64_t)s * o + pp) * v + ba) * dp + kk;
                 break;
             case 1:
-                aptr = p.G + ((int64_t)pp * v2 + row_swp) * dp + kk;
-                bptr = p.T2R + (((int64_t)s * o + q) * v + ba) * dp + kk;
+                aptr = Gm + ((int64_t)pp * v2 + row_swp) * dp + kk;
+                bptr = T2R + (((int64_t)s * o + q) * v + ba) * dp + kk;
                 break;
             case 2:
-                aptr = p.T2K + ((int64_t)pp * v2 + row_nat) * lp + kk;
-                bptr = p.AoN + (((int64_t)q * o + s) * v + ba) * lp + kk;
+                aptr = T2K + ((int64_t)pp * v2 + row_nat) * lp + kk;
+                bptr = AoN + (((int64_t)q * o + s) * v + ba) * lp + kk;
                 break;
             default:
-                aptr = p.T2K + ((int64_t)q * v2 + row_swp) * lp + kk;
-                bptr = p.AoN + (((int64_t)pp * o + s) * v + ba) * lp + kk;
+                aptr = T2K + ((int64_t)q * v2 + row_swp) * lp + kk;
+                bptr = AoN + (((int64_t)pp * o + s) * v + ba) * lp + kk;
                 break;
         }
     };
@@ -147,7 +152,7 @@ __global__ void __launch_bounds__(NT) ugemm_f64_kernel(const F64Params p) {
         __syncthreads();
     }
 
-    double *Ug = p.U + (int64_t)(tb * 3 + g) * v2 * vc;
+    double *Ug = static_cast<double *>(w.U) + sg.u_off + (int64_t)(tb * 3 + g) * v2 * vc;
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         const int a = a0 + ta * 4 + c;
@@ -164,21 +169,15 @@ __global__ void __launch_bounds__(NT) ugemm_f64_kernel(const F64Params p) {
 
 }  // namespace
 
-cudaError_t launch_ugemm_f64(const Operands &op, const GemmArgs &ga, cudaStream_t st) {
-    F64Params p;
-    p.dm = ga.dm;
-    p.G = static_cast<const double *>(op.G);
-    p.T2K = static_cast<const double *>(op.T2K);
-    p.T2R = static_cast<const double *>(op.T2R);
-    p.AoN = static_cast<const double *>(op.AoN);
-    p.tasks = ga.tasks;
-    p.task0 = ga.task0;
-    p.U = static_cast<double *>(ga.U);
-    const int64_t v2 = (int64_t)ga.dm.v * ga.dm.v;
-    const int64_t tiles = ((v2 + TP - 1) / TP) * ((ga.dm.v + TA - 1) / TA);
-    dim3 grid((unsigned)tiles, 1, (unsigned)(3 * ga.ntb));
-    if (tiles > 0x7fffffff || grid.z > 65535) return cudaErrorInvalidConfiguration;
-    ugemm_f64_kernel<<<grid, NT, 0, st>>>(p);
+int64_t f64_units_per_task(const Dims &dm) {
+    const int64_t v2 = (int64_t)dm.v * dm.v;
+    return 3 * ((v2 + TP - 1) / TP) * ((dm.v + TA - 1) / TA);
+}
+
+cudaError_t launch_ugemm_f64(const Wave &w, cudaStream_t st) {
+    if (w.n_gemm <= 0) return cudaSuccess;
+    if (w.n_gemm > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    ugemm_f64_kernel<<<(unsigned)w.n_gemm, NT, 0, st>>>(w);
     return cudaGetLastError();
 }
 

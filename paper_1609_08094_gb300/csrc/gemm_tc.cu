@@ -41,6 +41,7 @@
 
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "tcorr_internal.cuh"
 
@@ -50,8 +51,7 @@ namespace {
 constexpr int TC_THREADS = 320;
 constexpr int EPI_THREADS = 256;  // warps 2-9
 constexpr int STAGES = 4;
-constexpr int BM = 128;                 // pair rows per tile
-constexpr int PB = 8, PC = 16;          // pair tile = PB values of b x PC values of c
+constexpr int BM = 128;                 // pair rows per tile (pb values of b x pc values of c)
 constexpr int BN = 256;                 // a columns per accumulator
 constexpr int ROW_BYTES = 64;           // K bytes per smem row (SWIZZLE_64B span)
 constexpr int A_BYTES = BM * ROW_BYTES; // 8 KB
@@ -63,21 +63,7 @@ constexpr uint32_t WAIT_MIN_POLLS = 1u << 18;      // ... and at least this many
                                                    // spent off the GPU (pre-emption) never counts
 
 enum { MAP_G_NAT = 0, MAP_G_SWP, MAP_T2K_NAT, MAP_T2K_SWP, MAP_T2R, MAP_AON, NMAP };
-
-struct TcParams {
-    CUtensorMap map[NMAP][2];  // [operand map][hi, lo]
-    Dims dm;
-    const int *tasks;
-    int64_t task0;
-    float *U;
-    int *err;
-    int nbt, nct, npass, kv, ko, brows;
-    int64_t nitems;
-    uint32_t idesc_base;
-    uint32_t stage_tx;
-    int kb;            // K chunks per accumulator block
-    int inject_stall;  // testing only: CTA 0 withholds the loads of its first chunk
-};
+static_assert(NMAP == 6, "InstDesc::maps holds six operand maps");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -188,34 +174,43 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// A work item: (instance, task, group, pair tile, N pass), found from the
+// flat item number through the wave's segment table.
 struct Item {
+    const InstDesc *d;
+    int64_t u_off;   // element offset of the item's U block (task, group)
     int tb, g, bt, ct, n;
+    int s, p, q;     // (s; p, q) of the group
+    bool diag;       // i = j = k: no work
 };
-__device__ __forceinline__ Item decode(const TcParams &p, int64_t it) {
+__device__ __forceinline__ Item decode(const Wave &w, int64_t it) {
+    const Seg &sg = w.segs[seg_find(w.segs, w.nseg, it, [](const Seg &x) { return x.gemm0; })];
     Item r;
-    r.n = (int)(it % p.npass);
-    it /= p.npass;
-    r.ct = (int)(it % p.nct);
-    it /= p.nct;
-    r.bt = (int)(it % p.nbt);
-    it /= p.nbt;
-    r.g = (int)(it % 3);
-    r.tb = (int)(it / 3);
+    r.d = w.descs + sg.inst;
+    const InstDesc &d = *r.d;
+    int64_t x = it - sg.gemm0;
+    r.n = (int)(x % d.npass);
+    x /= d.npass;
+    r.ct = (int)(x % d.nct);
+    x /= d.nct;
+    r.bt = (int)(x % d.nbt);
+    x /= d.nbt;
+    r.g = (int)(x % 3);
+    r.tb = (int)(x / 3);
+    const int64_t v = d.dm.v;
+    r.u_off = sg.u_off + (int64_t)(r.tb * 3 + r.g) * v * v * d.dm.vc;
+    const int *tk = d.tasks + 3 * (sg.task0 + r.tb);
+    const int i = tk[0], j = tk[1], k = tk[2];
+    r.diag = (i == j && j == k);
+    if (r.g == 0) { r.s = i; r.p = j; r.q = k; }
+    else if (r.g == 1) { r.s = j; r.p = i; r.q = k; }
+    else { r.s = k; r.p = i; r.q = j; }
     return r;
 }
-// (s; p, q) of group g of the task
-__device__ __forceinline__ void group_indices(const TcParams &p, const Item &w, int &s, int &pp, int &q,
-                                              bool &diag) {
-    const int *tk = p.tasks + 3 * (p.task0 + w.tb);
-    const int i = tk[0], j = tk[1], k = tk[2];
-    diag = (i == j && j == k);
-    if (w.g == 0) { s = i; pp = j; q = k; }
-    else if (w.g == 1) { s = j; pp = i; q = k; }
-    else { s = k; pp = i; q = j; }
-}
+__device__ __forceinline__ int num_chunks(const InstDesc &d) { return 2 * d.kv + 2 * d.ko; }
 
 template <int KIND>
-__global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_constant__ Wave wv) {
     extern __shared__ __align__(1024) uint8_t smem_dyn[];
     __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
     __shared__ __align__(8) uint64_t bar_hfull[2], bar_hempty[2];
@@ -249,9 +244,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
     tc_fence_after();
     const uint32_t tmem = tmem_holder;
 
-    const int v = p.dm.v, o = p.dm.o;
-    const int nch = 2 * p.kv + 2 * p.ko;
     const int kch = ROW_BYTES / (KIND == 1 ? 4 : 2);
+    // instruction descriptor: D = F32, A/B = TF32 (2) or BF16 (1), K-major, M = 128
+    constexpr uint32_t fmt = KIND == 1 ? 2u : 1u;
+    constexpr uint32_t idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BM >> 4) << 24);
 
     if (warp == 0) {
         if (lane == 0) {
@@ -260,30 +256,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
             int last_phase[STAGES];
             for (int s = 0; s < STAGES; s++) last_phase[s] = -1;
             bool ok = true;
-            bool inject = p.inject_stall != 0 && blockIdx.x == 0;
-            for (int64_t it = blockIdx.x; it < p.nitems && ok; it += gridDim.x) {
-                const Item w = decode(p, it);
-                int s, pp, q;
-                bool diag;
-                group_indices(p, w, s, pp, q, diag);
-                if (diag) continue;
-                const int cb = w.bt * PB, cc = w.ct * PC, ca = w.n * BN;
+            bool inject = wv.inject_stall != 0 && blockIdx.x == 0;
+            for (int64_t it = blockIdx.x; it < wv.n_gemm && ok; it += gridDim.x) {
+                const Item w = decode(wv, it);
+                if (w.diag) continue;
+                const InstDesc &d = *w.d;
+                const int o = d.dm.o, kv = d.kv, ko = d.ko, nch = num_chunks(d);
+                const int s = w.s, pp = w.p, q = w.q;
+                const int cb = w.bt * d.pb, cc = w.ct * d.pc, ca = w.n * BN;
+                const uint32_t stage_tx = d.stage_tx;
                 for (int ch = 0; ch < nch; ch++) {
                     if (!mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1u, &abort_sh)) {
-                        fail(&abort_sh, p.err, DERR_TIMEOUT_EMPTY);
+                        fail(&abort_sh, wv.err, DERR_TIMEOUT_EMPTY);
                         ok = false;
                         break;
                     }
                     const uint32_t full = smem_u32(&bar_full[stage]);
-                    mbar_expect_tx(full, p.stage_tx);
+                    mbar_expect_tx(full, stage_tx);
                     last_phase[stage] = (int)phase;
                     const uint32_t sA = sbase + stage * STAGE_BYTES, sAl = sA + A_BYTES;
                     const uint32_t sB = sAl + A_BYTES, sBl = sB + B_BYTES;
                     int seg, kk;
-                    if (ch < p.kv) { seg = 0; kk = ch; }
-                    else if (ch < 2 * p.kv) { seg = 1; kk = ch - p.kv; }
-                    else if (ch < 2 * p.kv + p.ko) { seg = 2; kk = ch - 2 * p.kv; }
-                    else { seg = 3; kk = ch - 2 * p.kv - p.ko; }
+                    if (ch < kv) { seg = 0; kk = ch; }
+                    else if (ch < 2 * kv) { seg = 1; kk = ch - kv; }
+                    else if (ch < 2 * kv + ko) { seg = 2; kk = ch - 2 * kv; }
+                    else { seg = 3; kk = ch - 2 * kv - ko; }
                     const int k0 = kk * kch;
                     int amap, aslice, bmap, brow;
                     switch (seg) {
@@ -296,10 +293,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                         inject = false;
                         last_phase[stage] = -1;  // nothing in flight: the consumer's wait must expire
                     } else {
-                        tma_load_4d(sA, &p.map[amap][0], full, k0, cc, cb, aslice);
-                        tma_load_4d(sAl, &p.map[amap][1], full, k0, cc, cb, aslice);
-                        tma_load_3d(sB, &p.map[bmap][0], full, k0, ca, brow);
-                        tma_load_3d(sBl, &p.map[bmap][1], full, k0, ca, brow);
+                        tma_load_4d(sA, &d.maps[amap][0], full, k0, cc, cb, aslice);
+                        tma_load_4d(sAl, &d.maps[amap][1], full, k0, cc, cb, aslice);
+                        tma_load_3d(sB, &d.maps[bmap][0], full, k0, ca, brow);
+                        tma_load_3d(sBl, &d.maps[bmap][1], full, k0, ca, brow);
                     }
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
@@ -320,33 +317,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
             uint32_t phase = 0;
             uint32_t hblk = 0;  // K blocks issued so far: buffer hblk & 1, phase (hblk >> 1) & 1
             bool ok = true;
-            for (int64_t it = blockIdx.x; it < p.nitems && ok; it += gridDim.x) {
-                const Item w = decode(p, it);
-                int s, pp, q;
-                bool diag;
-                group_indices(p, w, s, pp, q, diag);
-                if (diag) continue;
-                const int nvalid = min(BN, v - w.n * BN);
+            for (int64_t it = blockIdx.x; it < wv.n_gemm && ok; it += gridDim.x) {
+                const Item w = decode(wv, it);
+                if (w.diag) continue;
+                const InstDesc &d = *w.d;
+                const int nch = num_chunks(d), kb = d.kb;
+                const int nvalid = min(BN, d.dm.v - w.n * BN);
                 const int N = (nvalid + 15) / 16 * 16;
-                const uint32_t idesc = p.idesc_base | ((uint32_t)(N >> 3) << 17);
+                const uint32_t idesc = idesc_base | ((uint32_t)(N >> 3) << 17);
                 // K blocks of kb chunks: the small hi*lo and lo*hi products of each
                 // chunk are issued as its data lands, the dominant hi*hi products of
                 // the whole block last, so that the truncation of every instruction
                 // acts on the smallest possible accumulator; the block's stages are
                 // released together once its last MMA is issued.
-                for (int c0 = 0; c0 < nch && ok; c0 += p.kb) {
-                    const int nb = min(p.kb, nch - c0);
+                for (int c0 = 0; c0 < nch && ok; c0 += kb) {
+                    const int nb = min(kb, nch - c0);
                     const uint32_t buf = hblk & 1u;
                     int st0 = stage;
                     for (int cb = 0; cb < nb; cb++) {
                         if (!mbar_wait(smem_u32(&bar_full[stage]), phase, &abort_sh)) {
-                            fail(&abort_sh, p.err, DERR_TIMEOUT_FULL);
+                            fail(&abort_sh, wv.err, DERR_TIMEOUT_FULL);
                             ok = false;
                             break;
                         }
                         if (cb == 0 &&
                             !mbar_wait(smem_u32(&bar_hempty[buf]), ((hblk >> 1) & 1u) ^ 1u, &abort_sh)) {
-                            fail(&abort_sh, p.err, DERR_TIMEOUT_TMEM);
+                            fail(&abort_sh, wv.err, DERR_TIMEOUT_TMEM);
                             ok = false;
                             break;
                         }
@@ -389,19 +385,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
         const int wq = warp & 3;              // TMEM lane quarter of this warp
         const int half = (warp - 2) >> 2;     // column half [half*128, half*128 + 128)
         const int row = wq * 32 + lane;       // accumulator row = pair in tile
-        const int lb = row / PC, lc = row % PC;
-        const int64_t v2 = (int64_t)v * v;
-        const int vc = p.dm.vc;
-        const int nhb = (nch + p.kb - 1) / p.kb;
         const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
         uint32_t hblk = 0;
         bool ok = true;
-        for (int64_t it = blockIdx.x; it < p.nitems && ok; it += gridDim.x) {
-            const Item w = decode(p, it);
-            int s, pp, q;
-            bool diag;
-            group_indices(p, w, s, pp, q, diag);
-            if (diag) continue;
+        for (int64_t it = blockIdx.x; it < wv.n_gemm && ok; it += gridDim.x) {
+            const Item w = decode(wv, it);
+            if (w.diag) continue;
+            const InstDesc &d = *w.d;
+            const int v = d.dm.v, vc = d.dm.vc;
+            const int nhb = (num_chunks(d) + d.kb - 1) / d.kb;
+            const int lb = row / d.pc, lc = row % d.pc;
             float total[128];
 #pragma unroll
             for (int j = 0; j < 128; j++) total[j] = 0.f;
@@ -425,17 +418,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                 hblk++;
             }
             if (!ok) {
-                if (lane == 0) fail(&abort_sh, p.err, DERR_TIMEOUT_TMEM);
+                if (lane == 0) fail(&abort_sh, wv.err, DERR_TIMEOUT_TMEM);
                 break;
             }
             // rows of 16 consecutive c per half warp: group 0 and 2 in their own
             // [a][b][c] order, group 1 at [b][a][c] (aligned with W, see tcorr_internal.cuh)
-            const int b = w.bt * PB + lb, c = w.ct * PC + lc;
+            const int b = w.bt * d.pb + lb, c = w.ct * d.pc + lc;
             if (b < v && c < v) {
                 const int a0 = w.n * BN + half * 128;
                 const int64_t stride = w.g == 1 ? (int64_t)vc : (int64_t)v * vc;
                 const int64_t base = w.g == 1 ? (int64_t)b * v * vc + c : (int64_t)b * vc + c;
-                float *Ug = p.U + (int64_t)(w.tb * 3 + w.g) * v2 * vc + base + (int64_t)a0 * stride;
+                float *Ug = static_cast<float *>(wv.U) + w.u_off + base + (int64_t)a0 * stride;
                 const int na = min(128, v - a0);
                 if (na == 128) {
 #pragma unroll
@@ -499,112 +492,102 @@ bool encode(CUtensorMap *m, CUtensorMapDataType dt, int rank, void *base, const 
 
 bool tc_supported(int cc_major, int cc_minor) { return cc_major == 10 && cc_minor == 3; }
 
-cudaError_t tc_build_tensor_maps(Handle *h, std::string &err) {
-    const int o = h->dm.o, v = h->dm.v, dp = h->dm.dp, lp = h->dm.lp;
-    const bool tf = h->prec == TCORR_TF32X3;
+cudaError_t tc_fill_desc(InstDesc &d, int prec, const Operands &op, int pb, int kb, std::string &err) {
+    if (pb != 4 && pb != 8 && pb != 16) {
+        err = "tensor-core pair tile: pb must be 4, 8 or 16";
+        return cudaErrorInvalidValue;
+    }
+    if (kb < 1 || kb > STAGES - 1) {  // a K block holds its stages until its last MMA
+        err = "tensor-core accumulator block: kb must be 1 .. 3";
+        return cudaErrorInvalidValue;
+    }
+    const int o = d.dm.o, v = d.dm.v, dp = d.dm.dp, lp = d.dm.lp;
+    const bool tf = prec == TCORR_TF32X3;
     const uint64_t eb = tf ? 4 : 2;
     const CUtensorMapDataType dt = tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    const uint32_t kch = ROW_BYTES / (uint32_t)eb;
-    const uint32_t brows = (uint32_t)std::min(BN, round_up(v, 16));
-    auto *maps = static_cast<CUtensorMap *>(aligned_alloc(64, sizeof(CUtensorMap) * NMAP * 2));
-    if (!maps) {
-        err = "host allocation failed";
-        return cudaErrorMemoryAllocation;
-    }
-    free(h->tmaps);
-    h->tmaps = maps;
+    const int kch = ROW_BYTES / (int)eb;
+    const int pc = BM / pb;
+    d.pb = pb;
+    d.pc = pc;
+    d.kb = kb;
+    d.nbt = (v + pb - 1) / pb;
+    d.nct = (v + pc - 1) / pc;
+    d.npass = (v + BN - 1) / BN;
+    d.kv = (v + kch - 1) / kch;
+    d.ko = (o + kch - 1) / kch;
+    d.brows = std::min(BN, round_up(v, 16));
+    d.stage_tx = (uint32_t)(2 * A_BYTES + 2 * d.brows * ROW_BYTES);
     const uint64_t V = v, O = o;
-    void *hi[4] = {h->op.G, h->op.T2K, h->op.T2R, h->op.AoN};
-    void *lo[4] = {h->op.Glo, h->op.T2Klo, h->op.T2Rlo, h->op.AoNlo};
+    const uint32_t bk = (uint32_t)kch, bpc = (uint32_t)pc, bpb = (uint32_t)pb, brows = (uint32_t)d.brows;
+    void *hi[4] = {op.G, op.T2K, op.T2R, op.AoN};
+    void *lo[4] = {op.Glo, op.T2Klo, op.T2Rlo, op.AoNlo};
     for (int part = 0; part < 2; part++) {
         void *const *src = part == 0 ? hi : lo;
         {   // G natural: (d, c, b, q) with c = y index, b = x index
             uint64_t dims[4] = {V, V, V, O};
             uint64_t st[3] = {dp * eb, V * dp * eb, V * V * dp * eb};
-            uint32_t box[4] = {kch, PC, PB, 1};
-            if (!encode(&maps[MAP_G_NAT * 2 + part], dt, 4, src[0], dims, st, box, err, "G")) return cudaErrorInvalidValue;
+            uint32_t box[4] = {bk, bpc, bpb, 1};
+            if (!encode(&d.maps[MAP_G_NAT][part], dt, 4, src[0], dims, st, box, err, "G")) return cudaErrorInvalidValue;
         }
         {   // G swapped: (d, c, b, q) with c = x index, b = y index
             uint64_t dims[4] = {V, V, V, O};
             uint64_t st[3] = {V * dp * eb, dp * eb, V * V * dp * eb};
-            uint32_t box[4] = {kch, PC, PB, 1};
-            if (!encode(&maps[MAP_G_SWP * 2 + part], dt, 4, src[0], dims, st, box, err, "G swapped"))
+            uint32_t box[4] = {bk, bpc, bpb, 1};
+            if (!encode(&d.maps[MAP_G_SWP][part], dt, 4, src[0], dims, st, box, err, "G swapped"))
                 return cudaErrorInvalidValue;
         }
         {   // T2K natural
             uint64_t dims[4] = {O, V, V, O};
             uint64_t st[3] = {lp * eb, V * lp * eb, V * V * lp * eb};
-            uint32_t box[4] = {kch, PC, PB, 1};
-            if (!encode(&maps[MAP_T2K_NAT * 2 + part], dt, 4, src[1], dims, st, box, err, "T2K")) return cudaErrorInvalidValue;
+            uint32_t box[4] = {bk, bpc, bpb, 1};
+            if (!encode(&d.maps[MAP_T2K_NAT][part], dt, 4, src[1], dims, st, box, err, "T2K")) return cudaErrorInvalidValue;
         }
         {   // T2K swapped
             uint64_t dims[4] = {O, V, V, O};
             uint64_t st[3] = {V * lp * eb, lp * eb, V * V * lp * eb};
-            uint32_t box[4] = {kch, PC, PB, 1};
-            if (!encode(&maps[MAP_T2K_SWP * 2 + part], dt, 4, src[1], dims, st, box, err, "T2K swapped"))
+            uint32_t box[4] = {bk, bpc, bpb, 1};
+            if (!encode(&d.maps[MAP_T2K_SWP][part], dt, 4, src[1], dims, st, box, err, "T2K swapped"))
                 return cudaErrorInvalidValue;
         }
         {   // T2R: (d, a, s*o+p)
             uint64_t dims[3] = {V, V, O * O};
             uint64_t st[2] = {dp * eb, V * dp * eb};
-            uint32_t box[3] = {kch, brows, 1};
-            if (!encode(&maps[MAP_T2R * 2 + part], dt, 3, src[2], dims, st, box, err, "T2R")) return cudaErrorInvalidValue;
+            uint32_t box[3] = {bk, brows, 1};
+            if (!encode(&d.maps[MAP_T2R][part], dt, 3, src[2], dims, st, box, err, "T2R")) return cudaErrorInvalidValue;
         }
         {   // AoN: (l, a, q*o+s)
             uint64_t dims[3] = {O, V, O * O};
             uint64_t st[2] = {lp * eb, V * lp * eb};
-            uint32_t box[3] = {kch, brows, 1};
-            if (!encode(&maps[MAP_AON * 2 + part], dt, 3, src[3], dims, st, box, err, "AoN")) return cudaErrorInvalidValue;
+            uint32_t box[3] = {bk, brows, 1};
+            if (!encode(&d.maps[MAP_AON][part], dt, 3, src[3], dims, st, box, err, "AoN")) return cudaErrorInvalidValue;
         }
     }
     return cudaSuccess;
 }
 
-cudaError_t launch_ugemm_tc(Handle *h, const GemmArgs &ga, cudaStream_t st) {
-    static_assert(sizeof(TcParams) < 4000, "kernel parameter block too large");
-    const bool tf = h->prec == TCORR_TF32X3;
-    const int v = ga.dm.v, o = ga.dm.o;
-    const int kch = ROW_BYTES / (tf ? 4 : 2);
-    TcParams p;
-    memcpy(p.map, h->tmaps, sizeof(p.map));
-    p.dm = ga.dm;
-    p.tasks = ga.tasks;
-    p.task0 = ga.task0;
-    p.U = static_cast<float *>(ga.U);
-    p.err = h->err;
-    p.nbt = (v + PB - 1) / PB;
-    p.nct = (v + PC - 1) / PC;
-    p.npass = (v + BN - 1) / BN;
-    p.kv = (v + kch - 1) / kch;
-    p.ko = (o + kch - 1) / kch;
-    p.brows = std::min(BN, round_up(v, 16));
-    p.nitems = (int64_t)ga.ntb * 3 * p.nbt * p.nct * p.npass;
-    // instruction descriptor: D = F32, A/B = TF32 (2) or BF16 (1), K-major, M = 128
-    const uint32_t fmt = tf ? 2u : 1u;
-    p.idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BM >> 4) << 24);
-    p.stage_tx = (uint32_t)(2 * A_BYTES + 2 * p.brows * ROW_BYTES);
-    p.kb = 2;  // chunks per accumulator block (at most STAGES - 1: a block holds its stages)
-    p.inject_stall = h->inject_stall;
-    const int grid = (int)std::min<int64_t>(h->sm_count, p.nitems);
+int64_t tc_units_per_task(const InstDesc &d) { return (int64_t)3 * d.nbt * d.nct * d.npass; }
+
+cudaError_t tc_prepare(int prec) {
+    static std::mutex mu;
+    static bool done[2] = {false, false};
+    std::lock_guard<std::mutex> lk(mu);
+    const int t = prec == TCORR_TF32X3 ? 0 : 1;
+    if (done[t]) return cudaSuccess;
+    const cudaError_t e = t == 0 ? cudaFuncSetAttribute(ugemm_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        SMEM_BYTES)
+                                 : cudaFuncSetAttribute(ugemm_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        SMEM_BYTES);
+    if (e == cudaSuccess) done[t] = true;
+    return e;
+}
+
+cudaError_t launch_ugemm_tc(int prec, int sm_count, const Wave &w, cudaStream_t st) {
+    const int grid = (int)std::min<int64_t>(sm_count, w.n_gemm);
     if (grid <= 0) return cudaSuccess;
-    cudaError_t e;
-    if (tf) {
-        static bool attr = false;
-        if (!attr) {
-            e = cudaFuncSetAttribute(ugemm_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        ugemm_tc_kernel<1><<<grid, TC_THREADS, SMEM_BYTES, st>>>(p);
-    } else {
-        static bool attr = false;
-        if (!attr) {
-            e = cudaFuncSetAttribute(ugemm_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        ugemm_tc_kernel<2><<<grid, TC_THREADS, SMEM_BYTES, st>>>(p);
-    }
+    const cudaError_t e = tc_prepare(prec);
+    if (e != cudaSuccess) return e;
+    if (prec == TCORR_TF32X3) ugemm_tc_kernel<1><<<grid, TC_THREADS, SMEM_BYTES, st>>>(w);
+    else ugemm_tc_kernel<2><<<grid, TC_THREADS, SMEM_BYTES, st>>>(w);
     return cudaGetLastError();
 }
 

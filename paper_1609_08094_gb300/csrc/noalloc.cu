@@ -29,20 +29,30 @@ constexpr size_t NA_U_BYTES = (size_t)3 * NA_VMAX * NA_VMAX * NA_VMAX * sizeof(d
 constexpr size_t NA_PART_OFF = NA_U_BYTES;
 constexpr size_t NA_TASK_OFF = NA_PART_OFF + (size_t)NA_NORB * 2 * sizeof(double);
 constexpr size_t NA_ORB_OFF = NA_TASK_OFF + 16;
-constexpr size_t NA_END = NA_ORB_OFF + (size_t)NA_NORB * 3 * sizeof(int);
+constexpr size_t NA_SEG_OFF = (NA_ORB_OFF + (size_t)NA_NORB * 3 * sizeof(int) + 63) / 64 * 64;
+constexpr size_t NA_DESC_OFF = (NA_SEG_OFF + sizeof(Seg) + alignof(InstDesc) - 1) / alignof(InstDesc) * alignof(InstDesc);
+constexpr size_t NA_END = NA_DESC_OFF + sizeof(InstDesc);
 static_assert(NA_END <= TCORR_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the declared size");
 static_assert(NA_VMAX % UPAD == 0, "maximum v must be a multiple of the U row padding");
 
 // The scratch: U [3][v][v][vc] doubles, orbit partials [norb][2] doubles,
-// the task (3 ints) and the block-orbit table [norb][3] ints.
+// the task (3 ints), the block-orbit table [norb][3] ints, and the work
+// description the shared epilogue kernels read (one segment, one instance).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TCORR_NOALLOC_SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 void *g_ptr[MAX_DEVICES] = {};
 
-// Writes the task and the block orbits A <= B <= C (blocks of NA_TE).
-__global__ void noalloc_tables_kernel(int *task, int *orb, int nb, int i, int j, int k) {
+// Writes the work description, the task and the block orbits A <= B <= C
+// (blocks of NA_TE) into the scratch.
+__global__ void noalloc_tables_kernel(const InstDesc d, const Seg sg, InstDesc *d_out, Seg *sg_out, int *task,
+                                      int *orb, int nb, int i, int j, int k) {
+    static_assert(sizeof(InstDesc) % 4 == 0 && sizeof(Seg) % 4 == 0, "word copy");
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&d);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(d_out);
+    for (int w = threadIdx.x; w < (int)(sizeof(InstDesc) / 4); w += blockDim.x) dst[w] = src[w];
+    if (threadIdx.x == 0) *sg_out = sg;
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     task[0] = i;
     task[1] = j;
@@ -173,15 +183,36 @@ extern "C" tcorr_status tcorr_task_energy_noalloc(int o, int v, const double *ep
     double *partials = reinterpret_cast<double *>(sc + NA_PART_OFF);
     int *task = reinterpret_cast<int *>(sc + NA_TASK_OFF);
     int *orbits = reinterpret_cast<int *>(sc + NA_ORB_OFF);
-    Dims dm{o, v, round_up(v, KPAD), round_up(o, KPAD), round_up(v, UPAD)};
+    Seg *seg = reinterpret_cast<Seg *>(sc + NA_SEG_OFF);
+    InstDesc *desc = reinterpret_cast<InstDesc *>(sc + NA_DESC_OFF);
     const int nb = (v + NA_TE - 1) / NA_TE;
-    const int norb = nb * (nb + 1) * (nb + 2) / 6;
-    noalloc_tables_kernel<<<1, 32, 0, st>>>(task, orbits, nb, i, j, k);
+    InstDesc d{};
+    d.dm = Dims{o, v, round_up(v, KPAD), round_up(o, KPAD), round_up(v, UPAD)};
+    d.norb = nb * (nb + 1) * (nb + 2) / 6;
+    d.eps_o = eps_occ;
+    d.eps_v = eps_vir;
+    d.t1 = t1;
+    d.ovov = ovov;
+    d.tasks = task;
+    d.orbits = orbits;
+    d.task_e = e_out;
+    Seg sg{};
+    sg.inst = 0;
+    sg.ntb = 1;
+    noalloc_tables_kernel<<<1, 128, 0, st>>>(d, sg, desc, seg, task, orbits, nb, i, j, k);
     const int64_t v2 = (int64_t)v * v;
     dim3 grid((unsigned)((v2 + CT_P - 1) / CT_P), (unsigned)((v + CT_A - 1) / CT_A), 3);
-    ugemm_f64_canon_kernel<<<grid, 256, 0, st>>>(o, v, dm.vc, t2, vvvo, ooov, i, j, k, U);
-    EpiArgs ea{dm, task, 0, 1, U, eps_occ, eps_vir, t1, ovov, nullptr, orbits, norb, NA_TE, partials, e_out};
-    if (launch_epilogue(TCORR_FP64, ea, st) != cudaSuccess) return TCORR_ECUDA;
-    if (launch_task_reduce(ea, st) != cudaSuccess) return TCORR_ECUDA;
+    ugemm_f64_canon_kernel<<<grid, 256, 0, st>>>(o, v, d.dm.vc, t2, vvvo, ooov, i, j, k, U);
+    Wave w{};
+    w.descs = desc;
+    w.segs = seg;
+    w.nseg = 1;
+    w.n_gemm = 0;
+    w.n_epi = d.norb;
+    w.n_red = 1;
+    w.U = U;
+    w.partials = partials;
+    if (launch_epilogue(TCORR_FP64, w, st) != cudaSuccess) return TCORR_ECUDA;
+    if (launch_task_reduce(w, st) != cudaSuccess) return TCORR_ECUDA;
     return cudaGetLastError() == cudaSuccess ? TCORR_OK : TCORR_ECUDA;
 }

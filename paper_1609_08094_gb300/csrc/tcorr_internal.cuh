@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libtcorr.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -56,47 +57,62 @@ struct Operands {
     void *Glo = nullptr, *T2Klo = nullptr, *T2Rlo = nullptr, *AoNlo = nullptr;  // lo part (mixed)
 };
 
-struct Handle {
-    Dims dm{};
-    int prec = TCORR_FP64;
-    int profile = 0;
-    int inject_stall = 0;   // testing: make a tensor-core pipeline wait expire
-    int batch = 1;          // tasks per batch
-    int sm_count = 0, cc_major = 0, cc_minor = 0;
-    cudaStream_t stream = nullptr;
-    size_t bytes = 0;       // device bytes held
+// ---- work description shared by all kernels ------------------------------
+// One problem ("instance") as the kernels see it.  Lives in device memory;
+// a single handle has one, a batch one per problem.  Aligned like its tensor
+// maps (alignof(CUtensorMap)), so an array of them keeps every map aligned.
+struct InstDesc {
+    CUtensorMap maps[6][2];   // tensor-core operand maps [G, G swapped, T2K, T2K swapped, T2R, AoN][hi, lo]
+    Dims dm;
+    int pb, pc;               // tensor-core pair tile: pb values of b x pc values of c (pb * pc = 128)
+    int kb;                   // K chunks per tensor-core accumulator block
+    int nbt, nct, npass, kv, ko, brows;
+    uint32_t stage_tx;        // TMA bytes per pipeline stage
+    int norb;                 // epilogue block orbits per task (cube edge 8)
+    const void *G, *T2K, *T2R, *AoN;  // FP64 operand layouts (FP64 W contractions)
+    const double *eps_o, *eps_v;
+    const void *t1, *ovov;    // FP64 or FP32 copies for the epilogue
+    const float *dev_f;       // FP32 block-relative virtual energies (mixed epilogue)
+    const int *tasks;         // [ntask][3]
+    const int *orbits;        // [norb][3]
+    double *task_e;           // [ntask][2]
+};
+static_assert(alignof(InstDesc) % 64 == 0 && sizeof(InstDesc) % alignof(InstDesc) == 0,
+              "tensor maps need (at least) 64-byte alignment in every array element");
 
-    Operands op;
-    double *eps_o = nullptr, *eps_v = nullptr;  // FP64
-    void *t1 = nullptr;      // FP64 or FP32 copy
-    void *ovov = nullptr;    // FP64 or FP32 copy [o][v][o][v]
-    float *dev_f = nullptr;  // FP32 block-relative virtual energies (mixed epilogue)
+// A contiguous run of one instance's tasks inside one launch ("wave").
+// The prefix counts let every kernel find its segment by binary search.
+struct Seg {
+    int inst;                 // index into the InstDesc array
+    int ntb;                  // tasks in the segment
+    int64_t task0;            // first task of the segment in the instance's list
+    int64_t u_off;            // element offset of the segment's U block: [ntb][3][v][v][vc]
+    int64_t gemm0;            // prefix of W-contraction work units
+    int64_t epi0;             // prefix of epilogue items (task, block orbit)
+    int64_t red0;             // prefix of tasks
+    int64_t part_off;         // double offset of the segment's orbit partials [ntb][norb][2]
+};
 
-    int64_t ntask = 0;
-    int *tasks = nullptr;          // device [ntask][3]
-    double *task_e = nullptr;      // device [ntask][2] (E4, E5 share)
-    void *U = nullptr;             // device scratch [batch][3][v][v][vc]
-    size_t u_task_bytes = 0;
-    int epi_te = 8;                // epilogue cube edge
-    int norb = 0;                  // block orbits per task
-    int *orbits = nullptr;         // device [norb][3]
-    double *partials = nullptr;    // device [batch][norb][2]
-    double *sums = nullptr;        // device [3]
-    double *h_sums = nullptr;      // pinned host [3]
-    int *err = nullptr;            // device error flags
-    int *h_err = nullptr;          // pinned host copy
+// last segment s with key(s) <= x (segments sorted by key, key(0) = 0)
+template <typename F>
+__device__ __forceinline__ int seg_find(const Seg *segs, int nseg, int64_t x, F key) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (key(segs[mid]) <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
-    // tcgen05 path
-    void *tmaps = nullptr;   // host-side tensor maps (CUtensorMap array), built at create
-
-    // profiling: event pairs recorded around launches, resolved after the
-    // call's final stream synchronisation (no sync inside the launch sequence)
-    struct Pending { int cls; cudaEvent_t a, b; };
-    std::vector<Pending> pending;
-    double k_ms[KC_COUNT] = {0, 0, 0, 0};
-    int64_t k_launch[KC_COUNT] = {0, 0, 0, 0};
-
-    std::string last_error;
+struct Wave {
+    const InstDesc *descs;    // device
+    const Seg *segs;          // device, nseg entries
+    int nseg;
+    int64_t n_gemm, n_epi, n_red;  // totals of the three work kinds
+    void *U;                  // device scratch
+    double *partials;         // device scratch
+    int *err;                 // device error flags
+    int inject_stall;
 };
 
 // ---- prep.cu -------------------------------------------------------------
@@ -113,39 +129,31 @@ cudaError_t launch_to_float(const double *in, float *out, int64_t n, cudaStream_
 cudaError_t launch_block_deltas(const double *eps_v, float *dev_f, int v, int te, cudaStream_t st);
 
 // ---- gemm_f64.cu ---------------------------------------------------------
-struct GemmArgs {
-    Dims dm;
-    const int *tasks;     // device task list
-    int64_t task0;        // first task index of the batch
-    int ntb;              // tasks in the batch
-    void *U;              // [ntb][3][v][v][vc]
-};
-cudaError_t launch_ugemm_f64(const Operands &op, const GemmArgs &ga, cudaStream_t st);
+// FP64 work units of a segment: ntb * 3 * pair tiles * a tiles
+int64_t f64_units_per_task(const Dims &dm);
+cudaError_t launch_ugemm_f64(const Wave &w, cudaStream_t st);
 
 // ---- epilogue.cu ---------------------------------------------------------
-struct EpiArgs {
-    Dims dm;
-    const int *tasks;
-    int64_t task0;
-    int ntb;
-    const void *U;
-    const double *eps_o, *eps_v;
-    const void *t1, *ovov;
-    const float *dev_f;
-    const int *orbits;
-    int norb;
-    int te;
-    double *partials;     // [ntb][norb][2]
-    double *task_e;       // [ntask][2]
+cudaError_t launch_epilogue(int prec, const Wave &w, cudaStream_t st);
+cudaError_t launch_task_reduce(const Wave &w, cudaStream_t st);
+// One range of one problem's task energies, summed (Kahan) into out[0..2] =
+// (E4, E5, E4 + E5) by launch_span_sums (one CTA per span).
+struct SumSpan {
+    const double *task_e;
+    int64_t first, count;
+    double *out;
 };
-cudaError_t launch_epilogue(int prec, const EpiArgs &ea, cudaStream_t st);
-cudaError_t launch_task_reduce(const EpiArgs &ea, cudaStream_t st);
-cudaError_t launch_range_sum(const double *task_e, int64_t first, int64_t count,
-                             double *sums, cudaStream_t st);
+cudaError_t launch_span_sums(const SumSpan *spans, int n, cudaStream_t st);
+int epilogue_orbits(int v);   // block orbits per task (cube edge 8)
 
 // ---- gemm_tc.cu ----------------------------------------------------------
 bool tc_supported(int cc_major, int cc_minor);
-cudaError_t tc_build_tensor_maps(Handle *h, std::string &err);
-cudaError_t launch_ugemm_tc(Handle *h, const GemmArgs &ga, cudaStream_t st);
+// fills the tensor-core fields of d (maps, tile shape, derived counts) for
+// the operand layouts in op; pb in {4, 8, 16}, kb in {1, 2}
+cudaError_t tc_fill_desc(InstDesc &d, int prec, const Operands &op, int pb, int kb, std::string &err);
+int64_t tc_units_per_task(const InstDesc &d);
+// sets the kernel attributes once per process (call before any stream capture)
+cudaError_t tc_prepare(int prec);
+cudaError_t launch_ugemm_tc(int prec, int sm_count, const Wave &w, cudaStream_t st);
 
 }  // namespace tcorr

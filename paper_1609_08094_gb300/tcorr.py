@@ -33,7 +33,16 @@ class TcorrError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("host_inputs", ctypes.c_int),
                 ("batch_tasks", ctypes.c_int), ("profile", ctypes.c_int),
-                ("test_stall", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("test_stall", ctypes.c_int), ("tune", ctypes.c_int),
+                ("eager", ctypes.c_int), ("wave_mb", ctypes.c_int)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("o", ctypes.c_int), ("v", ctypes.c_int),
+                ("eps_occ", ctypes.c_void_p), ("eps_vir", ctypes.c_void_p),
+                ("t1", ctypes.c_void_p), ("t2", ctypes.c_void_p),
+                ("vvvo", ctypes.c_void_p), ("ooov", ctypes.c_void_p),
+                ("ovov", ctypes.c_void_p)]
 
 
 def library_path() -> str:
@@ -75,6 +84,26 @@ def load():
         lib.tcorr_status_string.argtypes = [ctypes.c_int]
         lib.tcorr_version.restype = ctypes.c_int
         lib.tcorr_version.argtypes = []
+        bp = ctypes.c_void_p
+        lib.tcorr_batch_create.restype = ctypes.c_int
+        lib.tcorr_batch_create.argtypes = [ctypes.POINTER(bp), ctypes.c_int, ctypes.POINTER(Problem),
+                                           ctypes.POINTER(Opts), vp]
+        lib.tcorr_batch_size.restype = ctypes.c_int
+        lib.tcorr_batch_size.argtypes = [bp]
+        lib.tcorr_batch_energy.restype = ctypes.c_int
+        lib.tcorr_batch_energy.argtypes = [bp, dp]
+        lib.tcorr_batch_tile.restype = ctypes.c_int
+        lib.tcorr_batch_tile.argtypes = [bp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        lib.tcorr_batch_plan.restype = ctypes.c_int
+        lib.tcorr_batch_plan.argtypes = [bp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.tcorr_batch_kernel_times.restype = ctypes.c_int
+        lib.tcorr_batch_kernel_times.argtypes = [bp, dp, ctypes.POINTER(i64), ctypes.c_int]
+        lib.tcorr_batch_device_bytes.restype = i64
+        lib.tcorr_batch_device_bytes.argtypes = [bp]
+        lib.tcorr_batch_last_error.restype = ctypes.c_char_p
+        lib.tcorr_batch_last_error.argtypes = [bp]
+        lib.tcorr_batch_destroy.restype = ctypes.c_int
+        lib.tcorr_batch_destroy.argtypes = [bp]
         lib.tcorr_task_energy_noalloc.restype = ctypes.c_int
         lib.tcorr_task_energy_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp,
                                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
@@ -85,6 +114,9 @@ def load():
 EXPORTS = ("tcorr_create", "tcorr_energy", "tcorr_energy_range", "tcorr_num_tasks",
            "tcorr_task", "tcorr_kernel_times", "tcorr_device_bytes", "tcorr_destroy",
            "tcorr_last_error", "tcorr_status_string", "tcorr_version",
+           "tcorr_batch_create", "tcorr_batch_size", "tcorr_batch_energy", "tcorr_batch_tile",
+           "tcorr_batch_plan", "tcorr_batch_kernel_times", "tcorr_batch_device_bytes",
+           "tcorr_batch_last_error", "tcorr_batch_destroy",
            "tcorr_task_energy_noalloc")
 NOALLOC_MAX_V = 64
 
@@ -119,7 +151,7 @@ class Tcorr:
     None for torch's current stream (device inputs) / the default stream."""
 
     def __init__(self, o, v, eps_occ, eps_vir, t1, t2, vvvo, ooov, ovov, prec="fp64",
-                 batch_tasks=0, profile=False, stream=None, test_stall=False):
+                 batch_tasks=0, profile=False, stream=None, test_stall=False, tune=False):
         lib = load()
         arrays = dict(eps_occ=eps_occ, eps_vir=eps_vir, t1=t1, t2=t2, vvvo=vvvo, ooov=ooov,
                       ovov=ovov)
@@ -134,7 +166,7 @@ class Tcorr:
             prec = PREC[prec.lower()]
         opts = Opts(prec=int(prec), host_inputs=0 if on_device else 1,
                     batch_tasks=int(batch_tasks), profile=1 if profile else 0,
-                    test_stall=1 if test_stall else 0)
+                    test_stall=1 if test_stall else 0, tune=1 if tune else 0)
         if stream is None and on_device:
             import torch
             stream = torch.cuda.current_stream(t2.device)
@@ -193,6 +225,112 @@ class Tcorr:
     def close(self):
         if getattr(self, "_h", None):
             load().tcorr_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_ARRAY_NAMES = ("eps_occ", "eps_vir", "t1", "t2", "vvvo", "ooov", "ovov")
+
+
+class Batch:
+    """Many independent (T) problems of uneven (o, v) evaluated together
+    (tcorr_batch_*): their tasks share waves of the same kernels, and the
+    launch sequence is replayed from a CUDA graph after the first call.
+
+    ``problems``: a sequence of (o, v, eps_occ, eps_vir, t1, t2, vvvo, ooov,
+    ovov) tuples (or objects with ``o``, ``v`` and ``arrays()``), all on the
+    device or all on the host.  ``energy()`` returns an [n][3] array of
+    (E[4], E[5], E(T))."""
+
+    def __init__(self, problems, prec="fp64", batch_tasks=0, profile=False, stream=None,
+                 tune=False, eager=False, wave_mb=0):
+        lib = load()
+        items = []
+        for p in problems:
+            if hasattr(p, "arrays"):
+                items.append((p.o, p.v, *p.arrays()))
+            else:
+                items.append(tuple(p))
+        if not items:
+            raise ValueError("a batch needs at least one problem")
+        on_device = bool(getattr(items[0][5], "is_cuda", False))
+        arr = (Problem * len(items))()
+        keep = []
+        for n, it in enumerate(items):
+            o, v = int(it[0]), int(it[1])
+            shapes = dict(eps_occ=(o,), eps_vir=(v,), t1=(o, v), t2=(o, o, v, v),
+                          vvvo=(v, v, v, o), ooov=(o, o, o, v), ovov=(o, v, o, v))
+            ptrs = []
+            for name, a in zip(_ARRAY_NAMES, it[2:]):
+                _shape_check(f"problem {n} {name}", a, shapes[name])
+                ptrs.append(_pointer(f"problem {n} {name}", a, on_device))
+                keep.append(a)
+            arr[n] = Problem(o, v, *ptrs)
+        if isinstance(prec, str):
+            prec = PREC[prec.lower()]
+        opts = Opts(prec=int(prec), host_inputs=0 if on_device else 1,
+                    batch_tasks=int(batch_tasks), profile=1 if profile else 0,
+                    tune=1 if tune else 0, eager=1 if eager else 0, wave_mb=int(wave_mb))
+        if stream is None and on_device:
+            import torch
+            stream = torch.cuda.current_stream(items[0][5].device)
+        sptr = getattr(stream, "cuda_stream", stream) or 0
+        self._stream = stream
+        self.n, self.prec = len(items), int(prec)
+        self.shapes = [(int(it[0]), int(it[1])) for it in items]
+        h = ctypes.c_void_p()
+        st = lib.tcorr_batch_create(ctypes.byref(h), len(items), arr, ctypes.byref(opts),
+                                    ctypes.c_void_p(sptr))
+        if st != 0:
+            raise TcorrError(st, lib.tcorr_batch_last_error(None).decode())
+        self._h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise TcorrError(st, load().tcorr_batch_last_error(self._h).decode())
+
+    def energy(self) -> np.ndarray:
+        """[n][3] array: (E[4], E[5], E(T)) of every problem."""
+        e = np.zeros((self.n, 3), dtype=np.float64)
+        self._check(load().tcorr_batch_energy(self._h, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return e
+
+    def tile(self, idx: int):
+        """(pb, kb) of problem idx's tensor-core tile; (0, 0) for FP64."""
+        t = (ctypes.c_int * 2)()
+        self._check(load().tcorr_batch_tile(self._h, int(idx), t))
+        return tuple(t)
+
+    def plan(self):
+        """(waves, kernel launches) of one energy call."""
+        w, n = ctypes.c_int64(), ctypes.c_int64()
+        self._check(load().tcorr_batch_plan(self._h, ctypes.byref(w), ctypes.byref(n)))
+        return int(w.value), int(n.value)
+
+    def kernel_times(self, reset: bool = False):
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int64 * 4)()
+        self._check(load().tcorr_batch_kernel_times(self._h, ms, n, 1 if reset else 0))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load().tcorr_batch_device_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tcorr_batch_destroy(self._h)
             self._h = None
 
     def __enter__(self):

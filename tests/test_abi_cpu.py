@@ -40,7 +40,7 @@ def test_status_strings_and_version(lib):
     for i, s in enumerate(tcorr.STATUS):
         assert lib.tcorr_status_string(i).decode() == s
     assert lib.tcorr_status_string(99).decode() == "TCORR_UNKNOWN"
-    assert lib.tcorr_version() == 1
+    assert lib.tcorr_version() == 2
 
 
 def test_invalid_arguments_rejected_before_device_work(lib):
@@ -56,9 +56,11 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     assert b"NULL" in lib.tcorr_last_error(None) or len(lib.tcorr_last_error(None)) > 0
     bad = tcorr.Opts(prec=7)
     assert lib.tcorr_create(ctypes.byref(h), 2, 2, p, p, p, p, p, p, p, ctypes.byref(bad), None) == 1
-    res = tcorr.Opts()
-    res.reserved[2] = 1
-    assert lib.tcorr_create(ctypes.byref(h), 2, 2, p, p, p, p, p, p, p, ctypes.byref(res), None) == 1
+    for field, value in (("tune", 2), ("eager", -1), ("wave_mb", -5), ("test_stall", 3),
+                         ("host_inputs", 2), ("batch_tasks", -1)):
+        o = tcorr.Opts()
+        setattr(o, field, value)
+        assert lib.tcorr_create(ctypes.byref(h), 2, 2, p, p, p, p, p, p, p, ctypes.byref(o), None) == 1, field
     assert lib.tcorr_destroy(None) == 0
     assert lib.tcorr_num_tasks(None) == -1
     assert lib.tcorr_energy(None, None) == 1
@@ -68,3 +70,41 @@ def test_flop_count_definition():
     # 12 v^3 (v+o) per task, i=j=k tasks excluded
     assert tcorr.num_tasks(50) == 22100
     assert tcorr.algorithmic_flops(4, 20) == 12 * 20 ** 3 * 24 * (20 - 4)
+
+
+def test_batch_arguments_rejected_before_device_work(lib):
+    b = ctypes.c_void_p()
+    one = (ctypes.c_double * 1)()
+    p = ctypes.cast(one, ctypes.c_void_p).value
+    good = tcorr.Problem(2, 3, p, p, p, p, p, p, p)
+    arr = (tcorr.Problem * 2)(good, tcorr.Problem(2, 3, p, p, p, None, p, p, p))
+    assert lib.tcorr_batch_create(None, 1, arr, None, None) == 1
+    assert lib.tcorr_batch_create(ctypes.byref(b), 0, arr, None, None) == 1
+    assert lib.tcorr_batch_create(ctypes.byref(b), 1, None, None, None) == 1
+    assert lib.tcorr_batch_create(ctypes.byref(b), 2, arr, None, None) == 1  # problem 1: NULL t2
+    assert b"problem 1" in lib.tcorr_batch_last_error(None)
+    zero = (tcorr.Problem * 1)(tcorr.Problem(0, 3, p, p, p, p, p, p, p))
+    assert lib.tcorr_batch_create(ctypes.byref(b), 1, zero, None, None) == 1
+    big = (tcorr.Problem * 1)(tcorr.Problem(5000, 3, p, p, p, p, p, p, p))
+    assert lib.tcorr_batch_create(ctypes.byref(b), 1, big, None, None) == 5
+    bad = tcorr.Opts(prec=9)
+    assert lib.tcorr_batch_create(ctypes.byref(b), 1, arr, ctypes.byref(bad), None) == 1
+    assert b.value is None
+    assert lib.tcorr_batch_destroy(None) == 0
+    assert lib.tcorr_batch_size(None) == -1
+    assert lib.tcorr_batch_device_bytes(None) == -1
+    assert lib.tcorr_batch_energy(None, None) == 1
+    assert lib.tcorr_batch_plan(None, None, None) == 1
+    assert lib.tcorr_batch_tile(None, 0, None) == 1
+
+
+def test_option_struct_matches_header():
+    """The binding's Opts and Problem mirror the C structs field by field."""
+    text = open(os.path.join(ROOT, "include", "tcorr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\} tcorr_opts;", text, flags=re.S).group(1)
+    fields = re.findall(r"int\s+([a-z_]+)\s*;", body)
+    assert fields == [f for f, _ in tcorr.Opts._fields_]
+    body = re.search(r"typedef struct \{([^{}]*)\} tcorr_problem;", text, flags=re.S).group(1)
+    names = re.findall(r"\*?([a-z_][a-z_0-9]*)[,;]", body)
+    assert names == [f for f, _ in tcorr.Problem._fields_]
