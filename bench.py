@@ -41,6 +41,10 @@ FP64_PROBE_TFLOPS = 1.20     # DFMA throughput probe on this machine's GB300
 # v=450 from one ncu capture (profiles/ugemm_f64_kernel_o50_v450.md); valid
 # for this kernel version and workload only
 F64_GEMM_TRAFFIC_BYTES = {(50, 450): 5157372672 + 2182112768}
+# batched workload: n molecules, o ~ U{4..16}, v ~ U{20..120}, naux = 3(o+v),
+# per-molecule seeds seed+index; FP64 is timed on the first fp64_n of them
+# (the whole set is ~44 algorithmic TFLOP, ~40 s per pass on the FP64 pipe)
+BATCH = dict(n=256, seed=4, fp64_n=32)
 
 
 def parse():
@@ -60,6 +64,10 @@ def parse():
     ap.add_argument("--v", type=int, default=WORKLOAD["v"])
     ap.add_argument("--naux", type=int, default=WORKLOAD["naux"])
     ap.add_argument("--seed", type=int, default=WORKLOAD["seed"])
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-n", type=int, default=BATCH["n"])
+    ap.add_argument("--batch-fp64-n", type=int, default=BATCH["fp64_n"])
+    ap.add_argument("--wave-mb", type=int, default=0)
     return ap.parse_args()
 
 
@@ -337,6 +345,11 @@ def main():
                        "tcorr_energy_range, 3-double result read, tcorr_destroy"}
         del arrays
 
+    # ---- batched: many molecules of uneven size in one graph-replayed launch sequence
+    batched = None
+    if not args.no_batched:
+        batched = bench_batched(args, rank, world, stream)
+
     if rank != 0:
         return
     line = {
@@ -363,8 +376,116 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "mixed": mixed,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
+
+
+def bench_batched(args, rank, world, stream):
+    """The batched workload (BATCH): each rank takes its share of the
+    molecules (weak scaling, no collective).  Per precision: the whole set's
+    energies per step through one tcorr_batch handle (CUDA graph replay, tile
+    shapes from the measured autotuner), the same molecules one handle at a
+    time (the unbatched baseline, energy calls only), and the error of every
+    molecule against the FP64 path."""
+    import numpy as np
+    import torch
+
+    from paper_1609_08094_gb300 import synth, tcorr
+    shapes_all = synth.batch_shapes(args.batch_n, BATCH["seed"])
+    shapes = shapes_all[rank::world]
+    t0 = time.time()
+    insts = [synth.make_instance(o, v, naux, sd, device=torch.device("cuda", torch.cuda.current_device()))
+             for o, v, naux, sd in shapes]
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+
+    def flops(sub):
+        return sum((i.o * (i.o + 1) * (i.o + 2) // 6 - i.o) * 12.0 * i.v ** 3 * (i.v + i.o) for i in sub)
+
+    def ntask(sub):
+        return sum(i.o * (i.o + 1) * (i.o + 2) // 6 for i in sub)
+
+    def run(prec, sub, K, W):
+        with tcorr.Batch(sub, prec=prec, tune=(prec != "fp64"), stream=stream, wave_mb=args.wave_mb) as b:
+            e = None
+            for _ in range(W):       # the first call captures the graph
+                e = b.energy()
+            barrier(world)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(K):
+                e = b.energy()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = dist_max(ev0.elapsed_time(ev1), world) / K
+            waves, launches = b.plan()
+            tiles = sorted({b.tile(n)[0] for n in range(len(sub))})
+        # kernel shares from one profiled (direct-launch) pass
+        with tcorr.Batch(sub, prec=prec, tune=(prec != "fp64"), stream=stream, wave_mb=args.wave_mb,
+                         profile=True) as bp:
+            bp.energy()
+            kt = bp.kernel_times()
+        tot = sum(m for m, _ in kt.values())
+        return e, ms, waves, launches, tiles, kt, tot
+
+    def solo(prec, sub):
+        """Unbatched baseline: one handle per molecule, device time of the energy calls."""
+        total = 0.0
+        for inst in sub:
+            with tcorr.Tcorr.from_instance(inst, prec=prec, stream=stream) as t:
+                t.energy()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                t.energy()
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                total += ev0.elapsed_time(ev1)
+        return total
+
+    out = {"workload": f"{args.batch_n} molecules, o ~ U{{4..16}}, v ~ U{{20..120}}, naux = 3(o+v), "
+                       f"seeds {BATCH['seed']}+index; {len(shapes)} on this rank",
+           "generate_s": round(gen_s, 1), "precisions": {}}
+    pk = measured_peaks()
+    sub64 = insts[: max(1, args.batch_fp64_n // world)]
+    e64, ms64, wv, nl, _, kt, tot = run("fp64", sub64, K=1, W=1)
+    fl64 = flops(sub64) * world
+    out["precisions"]["fp64"] = {
+        "molecules": len(sub64) * world, "value": fl64 / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s",
+        "triples_per_s": ntask(sub64) * world / (ms64 * 1e-3), "ms_per_step": ms64, "steps": 1,
+        "waves": wv, "gpu_launches": nl,
+        "kernel_ms_share": {k: round(m / max(1e-9, tot), 4) for k, (m, _) in kt.items()},
+        "gemm_tflops": flops(sub64) / (kt["gemm"][0] * 1e-3) / 1e12,
+        "note": f"FP64 timed on the first {len(sub64) * world} molecules (one warm-up + one step)"}
+    ms_solo64 = solo("fp64", sub64)
+    out["precisions"]["fp64"]["unbatched_ms"] = ms_solo64
+    out["precisions"]["fp64"]["speedup_vs_unbatched"] = ms_solo64 / ms64
+    for prec in [x for x in args.precs.split(",") if x]:
+        try:
+            e, ms, wv, nl, tiles, kt, tot = run(prec, insts, K=args.steps, W=args.warmup)
+        except tcorr.TcorrError as err:
+            out["precisions"][prec] = {"unavailable": str(err)}
+            continue
+        fl = flops(insts) * world
+        peak = pk["bf16"] * (TF32_PER_BF16 if prec == "tf32x3" else 1.0)
+        gemm_tf = flops(insts) / (kt["gemm"][0] * 1e-3) / 1e12
+        # error against the FP64 path on the molecules that were timed in FP64
+        rel = np.abs(e[: len(sub64), 2] - e64[:, 2]) / np.abs(e64[:, 2])
+        ms_solo = solo(prec, insts)
+        out["precisions"][prec] = {
+            "molecules": len(insts) * world, "value": fl / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+            "triples_per_s": ntask(insts) * world / (ms * 1e-3), "ms_per_step": ms, "steps": args.steps,
+            "warmup": args.warmup, "waves": wv, "gpu_launches": nl, "tiles_pb": tiles,
+            "kernel_ms_share": {k: round(m / max(1e-9, tot), 4) for k, (m, _) in kt.items()},
+            "roofline": {"bound": "tensor", "kernel": f"ugemm_tc_kernel ({prec})", "achieved": gemm_tf,
+                         "peak": peak, "unit": "TFLOP/s", "frac": gemm_tf / peak, "traffic": None,
+                         "tensor_achieved": 3 * gemm_tf, "tensor_frac": 3 * gemm_tf / peak},
+            "max_rel_err_vs_fp64": float(rel.max()), "tol": 1e-6,
+            "unbatched_ms": ms_solo, "speedup_vs_unbatched": ms_solo / ms,
+            "speedup_vs_fp64_batched": (fl / (ms * 1e-3)) / (fl64 / (ms64 * 1e-3))}
+    return out
 
 
 def reference_arm(args):

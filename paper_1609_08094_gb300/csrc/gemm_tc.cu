@@ -50,14 +50,16 @@ namespace {
 
 constexpr int TC_THREADS = 320;
 constexpr int EPI_THREADS = 256;  // warps 2-9
-constexpr int STAGES = 4;
+constexpr int MAX_STAGES = 8;
 constexpr int BM = 128;                 // pair rows per tile (pb values of b x pc values of c)
 constexpr int BN = 256;                 // a columns per accumulator
 constexpr int ROW_BYTES = 64;           // K bytes per smem row (SWIZZLE_64B span)
 constexpr int A_BYTES = BM * ROW_BYTES; // 8 KB
 constexpr int B_BYTES = BN * ROW_BYTES; // 16 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+// The ring: 192 KB cut into stages of 2 A planes + 2 B planes of the wave's
+// largest B tile (brows rows): 4 stages for 256-row B tiles, up to 8 for small v
+constexpr int RING_BYTES = 4 * (2 * A_BYTES + 2 * B_BYTES);
+constexpr int SMEM_BYTES = RING_BYTES + 1024;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s of wall time per wait ...
 constexpr uint32_t WAIT_MIN_POLLS = 1u << 18;      // ... and at least this many polls, so that time
                                                    // spent off the GPU (pre-emption) never counts
@@ -160,47 +162,75 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
             "l"(a), "l"(b), "r"(idesc), "r"(acc));
     }
 }
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 consecutive accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// A work item: (instance, task, group, pair tile, N pass), found from the
-// flat item number through the wave's segment table.
-struct Item {
+struct SegCache {
+    int si;                    // cached segment (-1: none)
+    int64_t begin, end;        // its item range
     const InstDesc *d;
-    int64_t u_off;   // element offset of the item's U block (task, group)
+    int64_t task0, u_off;
+    int npass, nct, nbt;
+    int tcached;               // task (index in the segment) whose indices are cached
+    int ti, tj, tk;
+};
+__device__ __forceinline__ void seg_reset(SegCache &c) {
+    c.si = -1;
+    c.tcached = -1;
+}
+__device__ __forceinline__ void seg_update(const Wave &w, int64_t it, SegCache &c) {
+    if (c.si >= 0 && it < c.end) return;
+    int lo = c.si < 0 ? 0 : c.si, hi = w.nseg - 1;  // items only grow: search forward
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (w.segs[mid].gemm0 <= it) lo = mid; else hi = mid - 1;
+    }
+    const Seg &sg = w.segs[lo];
+    c.si = lo;
+    c.begin = sg.gemm0;
+    c.end = lo + 1 < w.nseg ? w.segs[lo + 1].gemm0 : w.n_gemm;
+    c.d = w.descs + sg.inst;
+    c.task0 = sg.task0;
+    c.u_off = sg.u_off;
+    c.npass = c.d->npass;
+    c.nct = c.d->nct;
+    c.nbt = c.d->nbt;
+    c.tcached = -1;
+}
+struct Item {
     int tb, g, bt, ct, n;
     int s, p, q;     // (s; p, q) of the group
     bool diag;       // i = j = k: no work
 };
-__device__ __forceinline__ Item decode(const Wave &w, int64_t it) {
-    const Seg &sg = w.segs[seg_find(w.segs, w.nseg, it, [](const Seg &x) { return x.gemm0; })];
+__device__ __forceinline__ Item decode(const Wave &w, int64_t it, SegCache &c) {
+    seg_update(w, it, c);
     Item r;
-    r.d = w.descs + sg.inst;
-    const InstDesc &d = *r.d;
-    int64_t x = it - sg.gemm0;
-    r.n = (int)(x % d.npass);
-    x /= d.npass;
-    r.ct = (int)(x % d.nct);
-    x /= d.nct;
-    r.bt = (int)(x % d.nbt);
-    x /= d.nbt;
+    int64_t x = it - c.begin;
+    r.n = (int)(x % c.npass);
+    x /= c.npass;
+    r.ct = (int)(x % c.nct);
+    x /= c.nct;
+    r.bt = (int)(x % c.nbt);
+    x /= c.nbt;
     r.g = (int)(x % 3);
     r.tb = (int)(x / 3);
-    const int64_t v = d.dm.v;
-    r.u_off = sg.u_off + (int64_t)(r.tb * 3 + r.g) * v * v * d.dm.vc;
-    const int *tk = d.tasks + 3 * (sg.task0 + r.tb);
-    const int i = tk[0], j = tk[1], k = tk[2];
+    if (r.tb != c.tcached) {
+        const int *tk = c.d->tasks + 3 * (c.task0 + r.tb);
+        c.ti = tk[0];
+        c.tj = tk[1];
+        c.tk = tk[2];
+        c.tcached = r.tb;
+    }
+    const int i = c.ti, j = c.tj, k = c.tk;
     r.diag = (i == j && j == k);
     if (r.g == 0) { r.s = i; r.p = j; r.q = k; }
     else if (r.g == 1) { r.s = j; r.p = i; r.q = k; }
@@ -208,20 +238,38 @@ __device__ __forceinline__ Item decode(const Wave &w, int64_t it) {
     return r;
 }
 __device__ __forceinline__ int num_chunks(const InstDesc &d) { return 2 * d.kv + 2 * d.ko; }
+// K steps of chunk ch that carry data: the K extent of each segment is padded
+// only to 16, so the last chunk of a segment may hold a single BF16 K step
+// (the rest of its 64-byte rows is TMA zero fill)
+template <int KIND>
+__device__ __forceinline__ int chunk_ksteps(const InstDesc &d, int ch) {
+    if constexpr (KIND == 1) {
+        return 2;  // TF32: 16 elements per chunk, always all data
+    } else {
+        int kk, kext;
+        if (ch < 2 * d.kv) { kk = ch < d.kv ? ch : ch - d.kv; kext = d.dm.dp; }
+        else { kk = ch - 2 * d.kv; kk = kk < d.ko ? kk : kk - d.ko; kext = d.dm.lp; }
+        return kext - kk * 32 >= 32 ? 2 : 1;
+    }
+}
 
 template <int KIND>
 __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_constant__ Wave wv) {
     extern __shared__ __align__(1024) uint8_t smem_dyn[];
-    __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
+    __shared__ __align__(8) uint64_t bar_full[MAX_STAGES], bar_empty[MAX_STAGES];
     __shared__ __align__(8) uint64_t bar_hfull[2], bar_hempty[2];
     __shared__ uint32_t tmem_holder;
     __shared__ volatile int abort_sh;
+    __shared__ SegCache ecache[EPI_THREADS / 32];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t sbase = (smem_u32(smem_dyn) + 1023u) & ~1023u;
+    const uint32_t b_plane = (uint32_t)wv.tc_brows * ROW_BYTES;     // multiple of 1024
+    const uint32_t stage_bytes = 2u * A_BYTES + 2u * b_plane;
+    const int nst = min(MAX_STAGES, (int)(RING_BYTES / stage_bytes));
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; s++) {
+        for (int s = 0; s < nst; s++) {
             mbar_init(smem_u32(&bar_full[s]), 1);
             mbar_init(smem_u32(&bar_empty[s]), 1);
         }
@@ -253,14 +301,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            int last_phase[STAGES];
-            for (int s = 0; s < STAGES; s++) last_phase[s] = -1;
+            int last_phase[MAX_STAGES];
+            for (int s = 0; s < MAX_STAGES; s++) last_phase[s] = -1;
             bool ok = true;
             bool inject = wv.inject_stall != 0 && blockIdx.x == 0;
+            SegCache sc;
+            seg_reset(sc);
             for (int64_t it = blockIdx.x; it < wv.n_gemm && ok; it += gridDim.x) {
-                const Item w = decode(wv, it);
+                const Item w = decode(wv, it, sc);
                 if (w.diag) continue;
-                const InstDesc &d = *w.d;
+                const InstDesc &d = *sc.d;
                 const int o = d.dm.o, kv = d.kv, ko = d.ko, nch = num_chunks(d);
                 const int s = w.s, pp = w.p, q = w.q;
                 const int cb = w.bt * d.pb, cc = w.ct * d.pc, ca = w.n * BN;
@@ -274,8 +324,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                     const uint32_t full = smem_u32(&bar_full[stage]);
                     mbar_expect_tx(full, stage_tx);
                     last_phase[stage] = (int)phase;
-                    const uint32_t sA = sbase + stage * STAGE_BYTES, sAl = sA + A_BYTES;
-                    const uint32_t sB = sAl + A_BYTES, sBl = sB + B_BYTES;
+                    const uint32_t sA = sbase + stage * stage_bytes, sAl = sA + A_BYTES;
+                    const uint32_t sB = sAl + A_BYTES, sBl = sB + b_plane;
                     int seg, kk;
                     if (ch < kv) { seg = 0; kk = ch; }
                     else if (ch < 2 * kv) { seg = 1; kk = ch - kv; }
@@ -298,11 +348,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                         tma_load_3d(sB, &d.maps[bmap][0], full, k0, ca, brow);
                         tma_load_3d(sBl, &d.maps[bmap][1], full, k0, ca, brow);
                     }
-                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    if (++stage == nst) { stage = 0; phase ^= 1u; }
                 }
             }
             if (!ok) {  // let this CTA's copies in flight land before exiting
-                for (int s = 0; s < STAGES; s++) {
+                for (int s = 0; s < nst; s++) {
                     if (last_phase[s] < 0) continue;
                     const uint64_t t0 = gtimer();
                     while (!mbar_test(smem_u32(&bar_full[s]), (uint32_t)last_phase[s]) &&
@@ -317,10 +367,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
             uint32_t phase = 0;
             uint32_t hblk = 0;  // K blocks issued so far: buffer hblk & 1, phase (hblk >> 1) & 1
             bool ok = true;
+            SegCache sc;
+            seg_reset(sc);
             for (int64_t it = blockIdx.x; it < wv.n_gemm && ok; it += gridDim.x) {
-                const Item w = decode(wv, it);
+                const Item w = decode(wv, it, sc);
                 if (w.diag) continue;
-                const InstDesc &d = *w.d;
+                const InstDesc &d = *sc.d;
                 const int nch = num_chunks(d), kb = d.kb;
                 const int nvalid = min(BN, d.dm.v - w.n * BN);
                 const int N = (nvalid + 15) / 16 * 16;
@@ -347,34 +399,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t d = tmem + buf * (uint32_t)BN;
-                        const uint32_t sA = sbase + stage * STAGE_BYTES, sAl = sA + A_BYTES;
-                        const uint32_t sB = sAl + A_BYTES, sBl = sB + B_BYTES;
-#pragma unroll
-                        for (int kk = 0; kk < 2; kk++) {
+                        const uint32_t dt = tmem + buf * (uint32_t)BN;
+                        const uint32_t sA = sbase + stage * stage_bytes, sAl = sA + A_BYTES;
+                        const uint32_t sB = sAl + A_BYTES, sBl = sB + b_plane;
+                        const int nks = chunk_ksteps<KIND>(d, c0 + cb);
+                        for (int kk = 0; kk < nks; kk++) {
                             const uint32_t off = kk * 32;
-                            tc_mma<KIND>(d, sdesc(sA + off), sdesc(sBl + off), idesc,
+                            tc_mma<KIND>(dt, sdesc(sA + off), sdesc(sBl + off), idesc,
                                          (cb > 0 || kk > 0) ? 1u : 0u);
-                            tc_mma<KIND>(d, sdesc(sAl + off), sdesc(sB + off), idesc, 1u);
+                            tc_mma<KIND>(dt, sdesc(sAl + off), sdesc(sB + off), idesc, 1u);
                         }
-                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                        if (++stage == nst) { stage = 0; phase ^= 1u; }
                     }
                     if (!ok) break;
-                    const uint32_t d = tmem + buf * (uint32_t)BN;
+                    const uint32_t dt = tmem + buf * (uint32_t)BN;
+                    // each stage is released (commit: arrives once every MMA issued
+                    // so far has completed) right after its last product is issued
                     int sj = st0;
                     for (int cb = 0; cb < nb; cb++) {
-                        const uint32_t sA = sbase + sj * STAGE_BYTES, sB = sA + 2 * A_BYTES;
-#pragma unroll
-                        for (int kk = 0; kk < 2; kk++) {
+                        const uint32_t sA = sbase + sj * stage_bytes, sB = sA + 2 * A_BYTES;
+                        const int nks = chunk_ksteps<KIND>(d, c0 + cb);
+                        for (int kk = 0; kk < nks; kk++) {
                             const uint32_t off = kk * 32;
-                            tc_mma<KIND>(d, sdesc(sA + off), sdesc(sB + off), idesc, 1u);
+                            tc_mma<KIND>(dt, sdesc(sA + off), sdesc(sB + off), idesc, 1u);
                         }
-                        if (++sj == STAGES) sj = 0;
-                    }
-                    sj = st0;
-                    for (int cb = 0; cb < nb; cb++) {
                         tc_commit(smem_u32(&bar_empty[sj]));
-                        if (++sj == STAGES) sj = 0;
+                        if (++sj == nst) sj = 0;
                     }
                     tc_commit(smem_u32(&bar_hfull[buf]));
                     hblk++;
@@ -383,18 +433,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
         }
     } else {
         const int wq = warp & 3;              // TMEM lane quarter of this warp
-        const int half = (warp - 2) >> 2;     // column half [half*128, half*128 + 128)
+        const int half = (warp - 2) >> 2;     // column half of the accumulator
         const int row = wq * 32 + lane;       // accumulator row = pair in tile
         const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
         uint32_t hblk = 0;
         bool ok = true;
+        // the decode cache of an epilogue warp lives in shared memory: in
+        // registers it would compete with the 128-column running total
+        SegCache &cs = ecache[warp - 2];
+        if (lane == 0) seg_reset(cs);
+        __syncwarp();
         for (int64_t it = blockIdx.x; it < wv.n_gemm && ok; it += gridDim.x) {
-            const Item w = decode(wv, it);
+            SegCache sc = cs;
+            const Item w = decode(wv, it, sc);
+            __syncwarp();
+            if (lane == 0) cs = sc;
+            __syncwarp();
             if (w.diag) continue;
-            const InstDesc &d = *w.d;
+            const InstDesc &d = *sc.d;
+            const int64_t u_seg = sc.u_off;
             const int v = d.dm.v, vc = d.dm.vc;
             const int nhb = (num_chunks(d) + d.kb - 1) / d.kb;
             const int lb = row / d.pc, lc = row % d.pc;
+            // the two warps of a lane quarter split the accumulator's N columns:
+            // 128 each for N > 128, else 32 or 64 each (only columns < N are read)
+            const int N = (min(BN, v - w.n * BN) + 15) / 16 * 16;
+            const int wh = N > 128 ? 128 : (N > 64 ? 64 : 32);
+            const int nld = wh / 32;
             float total[128];
 #pragma unroll
             for (int j = 0; j < 128; j++) total[j] = 0.f;
@@ -407,11 +472,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                 if (!good) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll
-                for (int c4 = 0; c4 < 4; c4++) {
-                    uint32_t r[32];
-                    tc_ld32(tmem + lane_off + buf * (uint32_t)BN + (uint32_t)(half * 128 + c4 * 32), r);
+                for (int c8 = 0; c8 < 8; c8++) {
+                    if (c8 < 2 * nld) {  // warp-uniform
+                        uint32_t r[16];
+                        tc_ld16(tmem + lane_off + buf * (uint32_t)BN + (uint32_t)(half * wh + c8 * 16), r);
 #pragma unroll
-                    for (int j = 0; j < 32; j++) total[c4 * 32 + j] += __uint_as_float(r[j]);
+                        for (int j = 0; j < 16; j++) total[c8 * 16 + j] += __uint_as_float(r[j]);
+                    }
                 }
                 tc_fence_before();
                 mbar_arrive(smem_u32(&bar_hempty[buf]));
@@ -425,11 +492,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
             // [a][b][c] order, group 1 at [b][a][c] (aligned with W, see tcorr_internal.cuh)
             const int b = w.bt * d.pb + lb, c = w.ct * d.pc + lc;
             if (b < v && c < v) {
-                const int a0 = w.n * BN + half * 128;
+                const int a0 = w.n * BN + half * wh;
                 const int64_t stride = w.g == 1 ? (int64_t)vc : (int64_t)v * vc;
                 const int64_t base = w.g == 1 ? (int64_t)b * v * vc + c : (int64_t)b * vc + c;
-                float *Ug = static_cast<float *>(wv.U) + w.u_off + base + (int64_t)a0 * stride;
-                const int na = min(128, v - a0);
+                const int64_t u_off = u_seg + (int64_t)(w.tb * 3 + w.g) * v * v * vc;
+                float *Ug = static_cast<float *>(wv.U) + u_off + base + (int64_t)a0 * stride;
+                const int na = min(wh, v - a0);
                 if (na == 128) {
 #pragma unroll
                     for (int j = 0; j < 128; j++) {
@@ -497,7 +565,7 @@ cudaError_t tc_fill_desc(InstDesc &d, int prec, const Operands &op, int pb, int 
         err = "tensor-core pair tile: pb must be 4, 8 or 16";
         return cudaErrorInvalidValue;
     }
-    if (kb < 1 || kb > STAGES - 1) {  // a K block holds its stages until its last MMA
+    if (kb < 1 || kb > 3) {  // a K block holds its stages until its last MMA (>= 4 stages)
         err = "tensor-core accumulator block: kb must be 1 .. 3";
         return cudaErrorInvalidValue;
     }
@@ -584,6 +652,7 @@ cudaError_t tc_prepare(int prec) {
 cudaError_t launch_ugemm_tc(int prec, int sm_count, const Wave &w, cudaStream_t st) {
     const int grid = (int)std::min<int64_t>(sm_count, w.n_gemm);
     if (grid <= 0) return cudaSuccess;
+    if (w.tc_brows < 16 || w.tc_brows > BN || w.tc_brows % 16 != 0) return cudaErrorInvalidValue;
     const cudaError_t e = tc_prepare(prec);
     if (e != cudaSuccess) return e;
     if (prec == TCORR_TF32X3) ugemm_tc_kernel<1><<<grid, TC_THREADS, SMEM_BYTES, st>>>(w);

@@ -386,6 +386,7 @@ struct Span {
 struct WaveRec {
     int seg0, nseg;
     int64_t n_gemm, n_epi, n_red;
+    int tc_brows;  // largest tensor-core B tile of the wave's problems
 };
 struct Plan {
     std::vector<Seg> segs;
@@ -395,11 +396,11 @@ struct Plan {
 
 Plan make_plan(const Exec &ex, const std::vector<Problem *> &pbs, const std::vector<Span> &spans) {
     Plan pl;
-    WaveRec cur{0, 0, 0, 0, 0};
+    WaveRec cur{0, 0, 0, 0, 0, 0};
     int64_t u_used = 0, p_used = 0, t_used = 0;
     auto close = [&]() {
         if (cur.nseg > 0) pl.waves.push_back(cur);
-        cur = WaveRec{(int)pl.segs.size(), 0, 0, 0, 0};
+        cur = WaveRec{(int)pl.segs.size(), 0, 0, 0, 0, 0};
         u_used = p_used = t_used = 0;
     };
     for (const Span &sp : spans) {
@@ -427,6 +428,7 @@ Plan make_plan(const Exec &ex, const std::vector<Problem *> &pbs, const std::vec
             s.part_off = p_used;
             pl.segs.push_back(s);
             cur.nseg++;
+            cur.tc_brows = std::max(cur.tc_brows, pb.desc.brows);
             cur.n_gemm += n * pb.gemm_units;
             cur.n_epi += n * pb.norb;
             cur.n_red += n;
@@ -487,6 +489,7 @@ void launch_plan(Exec &ex, const Plan &pl, const Seg *d_segs, const SumSpan *d_s
         w.partials = ex.partials;
         w.err = ex.err;
         w.inject_stall = ex.inject_stall;
+        w.tc_brows = wr.tc_brows;
         {
             Timer tm(ex, KC_GEMM);
             if (ex.prec == TCORR_FP64) CK(launch_ugemm_f64(w, st));
@@ -631,6 +634,7 @@ int tuned_pb(Exec &ex, Problem &pb) {
         w.n_gemm = n * tc_units_per_task(d);
         w.U = ex.U;
         w.err = ex.err;
+        w.tc_brows = d.brows;
         float ms_min = -1.f;
         for (int rep = 0; rep < 3; rep++) {
             CK(cudaEventRecord(e0, ex.stream));

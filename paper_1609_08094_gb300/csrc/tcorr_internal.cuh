@@ -113,6 +113,7 @@ struct Wave {
     double *partials;         // device scratch
     int *err;                 // device error flags
     int inject_stall;
+    int tc_brows;             // tensor-core path: largest B tile (rows) of the wave's problems
 };
 
 // ---- prep.cu -------------------------------------------------------------
