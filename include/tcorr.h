@@ -207,6 +207,81 @@ const char *tcorr_batch_last_error(tcorr_batch_t b);
 tcorr_status tcorr_batch_destroy(tcorr_batch_t b);
 
 /*
+ * Server: continuous batching of (T) jobs that arrive over time.
+ *
+ * Jobs are submitted at any time and queue in arrival order.  Each
+ * tcorr_server_step admits queued jobs, in order, while their device
+ * footprint fits the memory budget (layout preparation runs on the device,
+ * allocations are stream-ordered from the server's own pool), then enqueues
+ * one wave: tasks of every running job, each job first taking an equal share
+ * of the wave scratch and the remainder going to the oldest jobs, cut into
+ * segments of the same kernels the other handles use.  A job that arrives while
+ * others run joins the next wave; a job whose last tasks are in a wave gets
+ * its Kahan sum at the end of that wave and frees its memory when the wave
+ * completes.  Up to three waves are in flight; a step blocks only when all
+ * three are.  The per-task work does not depend on which other jobs share a
+ * wave, so a job's energies are bit-identical alone and in any mix.
+ * Device waits are bounded: a wave whose wait expires fails the jobs that were
+ * running (TCORR_ETIMEOUT) and the server continues with the next jobs.
+ */
+typedef struct tcorr_server_s *tcorr_server_t;
+
+typedef enum {
+    TCORR_JOB_QUEUED = 0,   /* submitted, not yet admitted */
+    TCORR_JOB_RUNNING = 1,  /* admitted: state resident on the device, tasks in waves */
+    TCORR_JOB_DONE = 2,     /* energies available from tcorr_server_poll */
+    TCORR_JOB_FAILED = 3    /* see the status of tcorr_server_poll */
+} tcorr_job_state;
+
+/*
+ * Create a server.  opts: prec, profile, test_stall as for tcorr_create;
+ * batch_tasks caps the tasks per wave (0 = 4096); wave_mb sizes the wave
+ * scratch (0 = 2048 MiB): a job whose single task needs more is rejected at
+ * submit.  hbm_bytes: device memory for admitted jobs' resident state
+ * (0 = 80% of the free memory after the server's own scratch).  host_inputs
+ * must be 0 (jobs pass device arrays).  Errors as for tcorr_create; the
+ * message of a failure is in tcorr_last_error(NULL).
+ */
+tcorr_status tcorr_server_create(tcorr_server_t *out, const tcorr_opts *opts, int64_t hbm_bytes,
+                                 void *stream);
+
+/*
+ * Queue a job; *id receives its identifier (0, 1, 2, ... in submit order).
+ * The problem's arrays are device pointers in the layouts of tcorr_create and
+ * must stay valid and unchanged until the job is DONE or FAILED.  Errors:
+ * EINVAL (bad problem), ENOMEM (footprint above the whole budget, or a
+ * single task above the wave scratch).  Does not touch the device.
+ */
+tcorr_status tcorr_server_submit(tcorr_server_t s, const tcorr_problem *p, int64_t *id);
+
+/*
+ * One scheduling step (see above).  *pending (may be NULL) receives the
+ * number of jobs not yet DONE or FAILED.  Returns an error only for a
+ * failure of the server itself; failed jobs are reported by poll.
+ */
+tcorr_status tcorr_server_step(tcorr_server_t s, int *pending);
+
+/*
+ * State of job id (non-blocking): *state a tcorr_job_state; when DONE,
+ * e_out (host, 3 doubles, may be NULL) receives E[4], E[5], E(T); when FAILED,
+ * *job_status (may be NULL) receives the job's tcorr_status.  EINVAL for an
+ * unknown id.
+ */
+tcorr_status tcorr_server_poll(tcorr_server_t s, int64_t id, int *state, double *e_out,
+                               int *job_status);
+
+/* Step until every submitted job is DONE or FAILED. */
+tcorr_status tcorr_server_drain(tcorr_server_t s);
+
+/* Counters (host, 8 int64): submitted, done, failed, running, queued,
+ * device bytes admitted now, peak bytes admitted, waves launched. */
+tcorr_status tcorr_server_stats(tcorr_server_t s, int64_t *stats);
+
+const char *tcorr_server_last_error(tcorr_server_t s);
+/* Waits for the waves in flight, then releases everything (NULL: no-op). */
+tcorr_status tcorr_server_destroy(tcorr_server_t s);
+
+/*
  * Allocation-free variant (the paper has no counterpart; it exists for
  * callers that must not allocate device memory: applications whose device
  * memory is owned entirely by their own pool or budget, and latency-sensitive

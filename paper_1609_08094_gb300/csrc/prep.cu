@@ -116,4 +116,29 @@ cudaError_t launch_block_deltas(const double *eps_v, float *dev_f, int v, int te
     return cudaGetLastError();
 }
 
+namespace {
+// Thread per leading index x: the sorted triples x <= y <= z of n values
+// start at offset sum_{x' < x} (n - x')(n - x' + 1) / 2.
+__global__ void sorted_triples_kernel(int n, int *out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    int64_t off = 0;
+    for (int xp = 0; xp < x; xp++) off += (int64_t)(n - xp) * (n - xp + 1) / 2;
+    int *w = out + 3 * off;
+    for (int y = x; y < n; y++)
+        for (int z = y; z < n; z++) {
+            w[0] = x;
+            w[1] = y;
+            w[2] = z;
+            w += 3;
+        }
+}
+}  // namespace
+
+cudaError_t launch_build_tables(int o, int nb, int *tasks, int *orbits, cudaStream_t st) {
+    sorted_triples_kernel<<<(o + 63) / 64, 64, 0, st>>>(o, tasks);
+    sorted_triples_kernel<<<(nb + 63) / 64, 64, 0, st>>>(nb, orbits);
+    return cudaGetLastError();
+}
+
 }  // namespace tcorr

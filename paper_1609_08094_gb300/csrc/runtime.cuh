@@ -1,0 +1,181 @@
+// Host runtime shared by the C ABI front ends (single problem, batch,
+// server): problem preparation (S0/S1), wave planning and the launch
+// sequence of S2-S5, allocation and error plumbing.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "tcorr_internal.cuh"
+
+namespace tcorr {
+namespace rt {
+
+constexpr int EPI_TE = 8;  // epilogue cube edge
+constexpr int TC_KB = 2;   // K chunks per tensor-core accumulator block (accuracy: see gemm_tc.cu)
+
+extern thread_local std::string g_create_error;
+
+struct Fail {
+    tcorr_status st;
+    std::string msg;
+};
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            throw Fail{TCORR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+// One (T) problem resident on the device: re-laid-out operands, epilogue
+// inputs, its task list and per-task energies, and its kernel descriptor.
+struct Problem {
+    Dims dm{};
+    Operands op;
+    double *eps_o = nullptr, *eps_v = nullptr;  // FP64
+    void *t1 = nullptr;      // FP64 or FP32 copy
+    void *ovov = nullptr;    // FP64 or FP32 copy [o][v][o][v]
+    float *dev_f = nullptr;  // FP32 block-relative virtual energies (mixed epilogue)
+    int64_t ntask = 0;
+    int *tasks = nullptr;      // device [ntask][3]
+    double *task_e = nullptr;  // device [ntask][2] (E4, E5 share)
+    int norb = 0;              // epilogue block orbits per task
+    int *orbits = nullptr;     // device [norb][3]
+    int64_t u_task = 0;        // U elements per task: 3 v v vc
+    int64_t gemm_units = 0;    // W-contraction work units per task
+    InstDesc desc{};           // host copy
+};
+
+// Execution state: stream, scratch, device descriptors, error flag, timers.
+struct Exec {
+    int prec = TCORR_FP64;
+    int profile = 0;
+    int inject_stall = 0;
+    int sm_count = 0, cc_major = 0, cc_minor = 0;
+    cudaStream_t stream = nullptr;
+    size_t bytes = 0;              // device bytes held
+    std::vector<void *> dev;       // every device allocation
+    std::vector<void *> host;      // every pinned host allocation
+    cudaMemPool_t pool = nullptr;  // set: stream-ordered allocations from this pool (freed in stream order)
+
+    void *U = nullptr;             // wave scratch
+    int64_t u_cap = 0;             // elements
+    double *partials = nullptr;    // orbit partials of a wave
+    int64_t part_cap = 0;          // doubles
+    int64_t wave_tasks = 0;        // tasks per wave (cap)
+    InstDesc *d_descs = nullptr;   // device [ninst]
+    int *err = nullptr, *h_err = nullptr;
+
+    // per-call tables: segments of every wave and the spans to sum
+    unsigned char *d_stage = nullptr, *h_stage = nullptr;
+    size_t stage_cap = 0;
+    double *d_sums = nullptr, *h_sums = nullptr;
+    int sums_cap = 0;
+
+    struct Pending { int cls; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    double k_ms[KC_COUNT] = {0, 0, 0, 0};
+    int64_t k_launch[KC_COUNT] = {0, 0, 0, 0};
+    std::string last_error;
+};
+
+template <typename T>
+void dalloc(Exec &ex, T *&ptr, size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = ex.pool ? cudaMallocFromPoolAsync(&p, bytes, ex.pool, ex.stream) : cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Fail{TCORR_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                     cudaGetErrorString(e)};
+    }
+    ex.dev.push_back(p);
+    ex.bytes += bytes;
+    ptr = static_cast<T *>(p);
+}
+
+template <typename T>
+void halloc(Exec &ex, T *&ptr, size_t bytes) {
+    void *p = nullptr;
+    CK(cudaMallocHost(&p, bytes ? bytes : 16));
+    ex.host.push_back(p);
+    ptr = static_cast<T *>(p);
+}
+
+struct Timer {
+    Exec &ex;
+    int cls;
+    cudaEvent_t a = nullptr;
+    Timer(Exec &e, int c) : ex(e), cls(c) {
+        if (!ex.profile) return;
+        CK(cudaEventCreate(&a));
+        CK(cudaEventRecord(a, ex.stream));
+    }
+    void stop() {
+        if (!ex.profile || !a) return;
+        cudaEvent_t b = nullptr;
+        CK(cudaEventCreate(&b));
+        CK(cudaEventRecord(b, ex.stream));
+        ex.pending.push_back({cls, a, b});
+        a = nullptr;
+    }
+    ~Timer() {
+        if (a) cudaEventDestroy(a);
+    }
+};
+
+// ---- waves ------------------------------------------------------------------
+// A span is a contiguous task range of one problem; a plan cuts the spans of
+// a call into waves that fit the scratch (U elements, orbit partials, task cap).
+struct Span {
+    int inst;
+    int64_t first, count;
+};
+struct WaveRec {
+    int seg0, nseg;
+    int64_t n_gemm, n_epi, n_red;
+    int tc_brows;  // largest tensor-core B tile of the wave's problems
+};
+struct Plan {
+    std::vector<Seg> segs;
+    std::vector<WaveRec> waves;
+    std::vector<SumSpan> sums;  // span n sums into d_sums[3n .. 3n+2] (out set at upload)
+};
+
+void dfree(Exec &ex, void *p, size_t bytes);
+void hfree(Exec &ex, void *p);
+void release(Exec &ex);
+const double *device_view(Exec &ex, const double *src, size_t n, bool host, double *&tmp);
+void free_tmp(Exec &ex, double *&tmp, size_t n);
+void resolve_timers(Exec &ex);
+int elem_kind(int prec);
+size_t elem_bytes(int prec);
+size_t u_elem_bytes(int prec);
+Dims make_dims(int o, int v);
+void build_operands(Exec &ex, Problem &pb, const double *t2, const double *vvvo, const double *ooov,
+                    bool host);
+void build_epilogue_inputs(Exec &ex, Problem &pb, const double *eps_occ, const double *eps_vir,
+                           const double *t1, const double *ovov, bool host);
+void build_schedule(Exec &ex, Problem &pb);
+void build_problem(Exec &ex, Problem &pb, int o, int v, const double *eps_occ, const double *eps_vir,
+                   const double *t1, const double *t2, const double *vvvo, const double *ooov,
+                   const double *ovov, bool host);
+size_t problem_bytes(const Dims &d, int prec);
+size_t host_staging_bytes(const Dims &d);
+int model_pb(int v);
+void fill_desc(Exec &ex, Problem &pb, int pbt);
+Plan make_plan(const Exec &ex, const std::vector<Problem *> &pbs, const std::vector<Span> &spans);
+void upload_plan(Exec &ex, Plan &pl, Seg *&d_segs, SumSpan *&d_spans);
+void launch_plan(Exec &ex, const Plan &pl, const Seg *d_segs, const SumSpan *d_spans, cudaStream_t st);
+void check_err_flag(Exec &ex);
+void finish_call(Exec &ex, int nspans);
+tcorr_status check_opts(const tcorr_opts &op, std::string &msg);
+bool sizes_supported(int o, int v);
+void init_exec(Exec &ex, const tcorr_opts &op, void *stream);
+void alloc_common(Exec &ex);
+void upload_descs(Exec &ex, const std::vector<Problem *> &pbs);
+int tuned_pb(Exec &ex, Problem &pb);
+
+}  // namespace rt
+}  // namespace tcorr

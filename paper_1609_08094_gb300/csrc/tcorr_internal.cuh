@@ -128,6 +128,10 @@ cudaError_t launch_transpose_pad(int kind, const double *in, void *out_hi, void 
 cudaError_t launch_to_float(const double *in, float *out, int64_t n, cudaStream_t st);
 // dev_f[x] = (float)(eps_v[block_start(x)] - eps_v[x]), block edge te
 cudaError_t launch_block_deltas(const double *eps_v, float *dev_f, int v, int te, cudaStream_t st);
+// tasks[n] = (i, j, k): the sorted occupied triples i <= j <= k of o orbitals
+// in lexicographic order; orbits[n] = (A, B, C): the sorted block triples
+// A <= B <= C of nb virtual blocks, lexicographic
+cudaError_t launch_build_tables(int o, int nb, int *tasks, int *orbits, cudaStream_t st);
 
 // ---- gemm_f64.cu ---------------------------------------------------------
 // FP64 work units of a segment: ntb * 3 * pair tiles * a tiles

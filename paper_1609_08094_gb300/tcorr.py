@@ -104,6 +104,24 @@ def load():
         lib.tcorr_batch_last_error.argtypes = [bp]
         lib.tcorr_batch_destroy.restype = ctypes.c_int
         lib.tcorr_batch_destroy.argtypes = [bp]
+        sp = ctypes.c_void_p
+        lib.tcorr_server_create.restype = ctypes.c_int
+        lib.tcorr_server_create.argtypes = [ctypes.POINTER(sp), ctypes.POINTER(Opts), i64, vp]
+        lib.tcorr_server_submit.restype = ctypes.c_int
+        lib.tcorr_server_submit.argtypes = [sp, ctypes.POINTER(Problem), ctypes.POINTER(i64)]
+        lib.tcorr_server_step.restype = ctypes.c_int
+        lib.tcorr_server_step.argtypes = [sp, ctypes.POINTER(ctypes.c_int)]
+        lib.tcorr_server_poll.restype = ctypes.c_int
+        lib.tcorr_server_poll.argtypes = [sp, i64, ctypes.POINTER(ctypes.c_int), dp,
+                                          ctypes.POINTER(ctypes.c_int)]
+        lib.tcorr_server_drain.restype = ctypes.c_int
+        lib.tcorr_server_drain.argtypes = [sp]
+        lib.tcorr_server_stats.restype = ctypes.c_int
+        lib.tcorr_server_stats.argtypes = [sp, ctypes.POINTER(i64)]
+        lib.tcorr_server_last_error.restype = ctypes.c_char_p
+        lib.tcorr_server_last_error.argtypes = [sp]
+        lib.tcorr_server_destroy.restype = ctypes.c_int
+        lib.tcorr_server_destroy.argtypes = [sp]
         lib.tcorr_task_energy_noalloc.restype = ctypes.c_int
         lib.tcorr_task_energy_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp,
                                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
@@ -117,7 +135,12 @@ EXPORTS = ("tcorr_create", "tcorr_energy", "tcorr_energy_range", "tcorr_num_task
            "tcorr_batch_create", "tcorr_batch_size", "tcorr_batch_energy", "tcorr_batch_tile",
            "tcorr_batch_plan", "tcorr_batch_kernel_times", "tcorr_batch_device_bytes",
            "tcorr_batch_last_error", "tcorr_batch_destroy",
+           "tcorr_server_create", "tcorr_server_submit", "tcorr_server_step", "tcorr_server_poll",
+           "tcorr_server_drain", "tcorr_server_stats", "tcorr_server_last_error",
+           "tcorr_server_destroy",
            "tcorr_task_energy_noalloc")
+JOB_STATES = ("queued", "running", "done", "failed")
+SERVER_STATS = ("submitted", "done", "failed", "running", "queued", "bytes", "peak_bytes", "waves")
 NOALLOC_MAX_V = 64
 
 
@@ -332,6 +355,101 @@ class Batch:
         if getattr(self, "_h", None):
             load().tcorr_batch_destroy(self._h)
             self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous batching of (T) jobs (tcorr_server_*).  ``submit`` queues a
+    job (device arrays that must stay alive until it is done; this object
+    keeps references until then), ``step`` admits what fits the memory budget
+    and enqueues one wave of tasks from every running job, ``poll`` reports a
+    job's state and energies.  ``hbm_bytes``: memory budget for admitted
+    jobs (0 = 80% of free memory)."""
+
+    def __init__(self, prec="bf16x3", hbm_bytes=0, wave_mb=0, batch_tasks=0, profile=False,
+                 stream=None, test_stall=False):
+        lib = load()
+        if isinstance(prec, str):
+            prec = PREC[prec.lower()]
+        opts = Opts(prec=int(prec), host_inputs=0, batch_tasks=int(batch_tasks),
+                    profile=1 if profile else 0, test_stall=1 if test_stall else 0,
+                    wave_mb=int(wave_mb))
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream()
+        sptr = getattr(stream, "cuda_stream", stream) or 0
+        self._stream = stream
+        self.prec = int(prec)
+        self._keep = {}
+        h = ctypes.c_void_p()
+        st = lib.tcorr_server_create(ctypes.byref(h), ctypes.byref(opts), int(hbm_bytes),
+                                     ctypes.c_void_p(sptr))
+        if st != 0:
+            raise TcorrError(st, lib.tcorr_server_last_error(None).decode())
+        self._h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise TcorrError(st, load().tcorr_server_last_error(self._h).decode())
+
+    def submit(self, problem) -> int:
+        """Queue a job: an Instance (device arrays) or an (o, v, eps_occ, ...,
+        ovov) tuple.  Returns the job id."""
+        it = (problem.o, problem.v, *problem.arrays()) if hasattr(problem, "arrays") else tuple(problem)
+        o, v = int(it[0]), int(it[1])
+        shapes = dict(eps_occ=(o,), eps_vir=(v,), t1=(o, v), t2=(o, o, v, v),
+                      vvvo=(v, v, v, o), ooov=(o, o, o, v), ovov=(o, v, o, v))
+        ptrs = []
+        for name, a in zip(_ARRAY_NAMES, it[2:]):
+            _shape_check(name, a, shapes[name])
+            ptrs.append(_pointer(name, a, True))
+        pr = Problem(o, v, *ptrs)
+        jid = ctypes.c_int64()
+        self._check(load().tcorr_server_submit(self._h, ctypes.byref(pr), ctypes.byref(jid)))
+        self._keep[jid.value] = it
+        return int(jid.value)
+
+    def step(self) -> int:
+        """One scheduling step; returns the number of jobs not yet finished."""
+        n = ctypes.c_int()
+        self._check(load().tcorr_server_step(self._h, ctypes.byref(n)))
+        return int(n.value)
+
+    def poll(self, jid: int):
+        """(state, energies or None, status): state in JOB_STATES."""
+        st = ctypes.c_int()
+        js = ctypes.c_int()
+        e = (ctypes.c_double * 3)()
+        self._check(load().tcorr_server_poll(self._h, int(jid), ctypes.byref(st), e, ctypes.byref(js)))
+        state = JOB_STATES[st.value]
+        if state in ("done", "failed"):
+            self._keep.pop(int(jid), None)
+        return state, (tuple(e) if state == "done" else None), int(js.value)
+
+    def drain(self):
+        self._check(load().tcorr_server_drain(self._h))
+
+    def stats(self):
+        a = (ctypes.c_int64 * 8)()
+        self._check(load().tcorr_server_stats(self._h, a))
+        return dict(zip(SERVER_STATS, (int(x) for x in a)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tcorr_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
 
     def __enter__(self):
         return self

@@ -108,3 +108,23 @@ def test_option_struct_matches_header():
     body = re.search(r"typedef struct \{([^{}]*)\} tcorr_problem;", text, flags=re.S).group(1)
     names = re.findall(r"\*?([a-z_][a-z_0-9]*)[,;]", body)
     assert names == [f for f, _ in tcorr.Problem._fields_]
+
+
+def test_server_arguments_rejected_before_device_work(lib):
+    sv = ctypes.c_void_p()
+    assert lib.tcorr_server_create(None, None, 0, None) == 1
+    host = tcorr.Opts(host_inputs=1)
+    assert lib.tcorr_server_create(ctypes.byref(sv), ctypes.byref(host), 0, None) == 1
+    assert lib.tcorr_server_create(ctypes.byref(sv), None, -1, None) == 1
+    bad = tcorr.Opts(prec=5)
+    assert lib.tcorr_server_create(ctypes.byref(sv), ctypes.byref(bad), 0, None) == 1
+    assert sv.value is None
+    assert len(lib.tcorr_server_last_error(None)) > 0
+    jid = ctypes.c_int64()
+    st = ctypes.c_int()
+    assert lib.tcorr_server_submit(None, None, ctypes.byref(jid)) == 1
+    assert lib.tcorr_server_step(None, None) == 1
+    assert lib.tcorr_server_poll(None, 0, ctypes.byref(st), None, None) == 1
+    assert lib.tcorr_server_drain(None) == 1
+    assert lib.tcorr_server_stats(None, None) == 1
+    assert lib.tcorr_server_destroy(None) == 0
