@@ -40,11 +40,16 @@ FP64_PROBE_TFLOPS = 1.20     # DFMA throughput probe on this machine's GB300
 # DRAM read+write bytes of one full-task launch of ugemm_f64_kernel at o=50,
 # v=450 from one ncu capture (profiles/ugemm_f64_kernel_o50_v450.md); valid
 # for this kernel version and workload only
-F64_GEMM_TRAFFIC_BYTES = {(50, 450): 5157372672 + 2182112768}
+F64_GEMM_TRAFFIC_BYTES = {(50, 450): 5146864384 + 2179871488}
 # batched workload: n molecules, o ~ U{4..16}, v ~ U{20..120}, naux = 3(o+v),
 # per-molecule seeds seed+index; FP64 is timed on the first fp64_n of them
 # (the whole set is ~44 algorithmic TFLOP, ~40 s per pass on the FP64 pipe)
 BATCH = dict(n=256, seed=4, fp64_n=32)
+# served workload: requests with o ~ U{4..40}, v ~ U{20..300}, each the
+# sub-problem (a window of o occupied and v virtual orbitals) of one seeded
+# o=40, v=300, naux=1020 system; Poisson arrivals at 0.7x the throughput
+# measured on a closed calibration batch; mixed precision
+SERVE = dict(o_max=40, v_max=300, naux=1020, seed=5, n=48, calib=12, load=0.7, prec="bf16x3")
 
 
 def parse():
@@ -68,6 +73,9 @@ def parse():
     ap.add_argument("--batch-n", type=int, default=BATCH["n"])
     ap.add_argument("--batch-fp64-n", type=int, default=BATCH["fp64_n"])
     ap.add_argument("--wave-mb", type=int, default=0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-n", type=int, default=SERVE["n"])
+    ap.add_argument("--serve-prec", default=SERVE["prec"])
     return ap.parse_args()
 
 
@@ -350,6 +358,10 @@ def main():
     if not args.no_batched:
         batched = bench_batched(args, rank, world, stream)
 
+    serving = None
+    if not args.no_serving:
+        serving = bench_serving(args, rank, world, stream)
+
     if rank != 0:
         return
     line = {
@@ -377,6 +389,7 @@ def main():
         "e2e": e2e,
         "mixed": mixed,
         "batched": batched,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
 
@@ -486,6 +499,112 @@ def bench_batched(args, rank, world, stream):
             "unbatched_ms": ms_solo, "speedup_vs_unbatched": ms_solo / ms,
             "speedup_vs_fp64_batched": (fl / (ms * 1e-3)) / (fl64 / (ms64 * 1e-3))}
     return out
+
+
+def serve_requests(n, seed, o_max, v_max):
+    """(o, v, i0, a0) of n requests: sizes uniform, windows at uniform offsets."""
+    from paper_1609_08094_gb300 import synth
+    u = [synth.uniform(seed, 20 + k, n) for k in range(4)]
+    out = []
+    for r in range(n):
+        o = 4 + int(u[0][r] * (o_max - 4 + 1))
+        v = 20 + int(u[1][r] * (v_max - 20 + 1))
+        i0 = int(u[2][r] * (o_max - o + 1))
+        a0 = int(u[3][r] * (v_max - v + 1))
+        out.append((o, v, i0, a0))
+    return out
+
+
+def window(base, o, v, i0, a0):
+    """The sub-problem of occupied i0..i0+o-1 and virtual a0..a0+v-1 (device copies)."""
+    oi, va = slice(i0, i0 + o), slice(a0, a0 + v)
+    arr = (base.eps_occ[oi], base.eps_vir[va], base.t1[oi, va], base.t2[oi, oi, va, va],
+           base.vvvo[va, va, va, oi], base.ooov[oi, oi, oi, va], base.ovov[oi, va, oi, va])
+    return (o, v, *[a.contiguous() for a in arr])
+
+
+def req_flops(o, v):
+    return (o * (o + 1) * (o + 2) // 6 - o) * 12.0 * v ** 3 * (v + o)
+
+
+def bench_serving(args, rank, world, stream):
+    """The served workload (SERVE) through tcorr_server: a closed calibration
+    batch measures the saturated throughput, then a Poisson stream at 0.7x of
+    it; latency = completion (observed by polling) - scheduled arrival.  Each
+    rank serves its own stream (replicas)."""
+    import numpy as np
+    import torch
+
+    from paper_1609_08094_gb300 import synth, tcorr
+    cfg = SERVE
+    t0 = time.time()
+    base = synth.make_instance(cfg["o_max"], cfg["v_max"], cfg["naux"], cfg["seed"] + rank,
+                               device=torch.device("cuda", torch.cuda.current_device()))
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    reqs = serve_requests(args.serve_n + cfg["calib"], cfg["seed"] + 100 * rank, cfg["o_max"], cfg["v_max"])
+    calib, stream_reqs = reqs[: cfg["calib"]], reqs[cfg["calib"]:]
+    prec = args.serve_prec
+    # mean work per request of the size distribution (large sample of the same law)
+    dist = serve_requests(20000, cfg["seed"] + 7, cfg["o_max"], cfg["v_max"])
+    mean_fl = float(np.mean([req_flops(o, v) for o, v, _, _ in dist]))
+
+    with tcorr.Server(prec=prec, stream=stream) as srv:
+        # closed batch: everything submitted at once -> saturated throughput
+        tc0 = time.perf_counter()
+        ids = [srv.submit(window(base, *r)) for r in calib]
+        srv.drain()
+        calib_s = time.perf_counter() - tc0
+        assert all(srv.poll(i)[0] == "done" for i in ids)
+        sat = sum(req_flops(o, v) for o, v, _, _ in calib) / calib_s   # flop/s
+        lam = cfg["load"] * sat / mean_fl                                # requests/s
+        gaps = -np.log(1.0 - synth.uniform(cfg["seed"] + 100 * rank, 30, len(stream_reqs))) / lam
+        arrive = np.cumsum(gaps)
+        barrier(world)
+        st0 = srv.stats()
+        t_start = time.perf_counter()
+        nxt, live, done_at, res = 0, {}, {}, {}
+        while len(done_at) < len(stream_reqs):
+            now = time.perf_counter() - t_start
+            while nxt < len(stream_reqs) and arrive[nxt] <= now:
+                live[srv.submit(window(base, *stream_reqs[nxt]))] = nxt
+                nxt += 1
+            pending = srv.step()
+            now = time.perf_counter() - t_start
+            for jid, k in list(live.items()):
+                state, e, status = srv.poll(jid)
+                if state in ("done", "failed"):
+                    done_at[k] = now
+                    res[k] = (state, e, status)
+                    del live[jid]
+            if pending == 0 and nxt < len(stream_reqs):
+                time.sleep(max(0.0, min(0.01, arrive[nxt] - (time.perf_counter() - t_start))))
+        makespan = max(done_at.values())
+        st1 = srv.stats()
+    lat = np.array([done_at[k] - arrive[k] for k in range(len(stream_reqs))])
+    ok = sum(1 for r in res.values() if r[0] == "done")
+    # a sample of the served jobs again, each alone: identical energies
+    same = 0
+    sample = list(range(0, len(stream_reqs), max(1, len(stream_reqs) // 4)))[:4]
+    with tcorr.Server(prec=prec, stream=stream) as solo:
+        for k in sample:
+            jid = solo.submit(window(base, *stream_reqs[k]))
+            solo.drain()
+            same += int(solo.poll(jid)[1] == res[k][1])
+    fl = sum(req_flops(o, v) for o, v, _, _ in stream_reqs)
+    makespan = dist_max(makespan, world)
+    return {"workload": f"{len(stream_reqs)} requests per GPU, o ~ U{{4..{cfg['o_max']}}}, "
+                        f"v ~ U{{20..{cfg['v_max']}}}, windows of one o={cfg['o_max']} v={cfg['v_max']} "
+                        f"naux={cfg['naux']} system (seed {cfg['seed']}), Poisson arrivals at "
+                        f"{cfg['load']}x the calibrated saturated throughput, {prec}",
+            "requests": len(stream_reqs) * world, "done": ok, "failed": len(res) - ok,
+            "lambda_req_per_s": lam, "saturated_tflops": sat / 1e12, "calibration_requests": len(calib),
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean()), "max": float(lat.max())},
+            "throughput": {"requests_per_s": len(stream_reqs) * world / makespan,
+                           "tflops": fl * world / makespan / 1e12, "makespan_s": makespan},
+            "waves": st1["waves"] - st0["waves"], "peak_admitted_bytes": st1["peak_bytes"],
+            "solo_vs_mixed_identical": f"{same}/{len(sample)}", "generate_s": round(gen_s, 1)}
 
 
 def reference_arm(args):

@@ -162,7 +162,8 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
             "l"(a), "l"(b), "r"(idesc), "r"(acc));
     }
 }
-// 16 consecutive accumulator columns of this warp's 32 TMEM lanes
+// 16 consecutive accumulator columns of this warp's 32 TMEM lanes (the
+// caller waits with tc_wait_ld before reading r)
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -171,8 +172,8 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 struct SegCache {
     int si;                    // cached segment (-1: none)
@@ -240,15 +241,16 @@ __device__ __forceinline__ Item decode(const Wave &w, int64_t it, SegCache &c) {
 __device__ __forceinline__ int num_chunks(const InstDesc &d) { return 2 * d.kv + 2 * d.ko; }
 // K steps of chunk ch that carry data: the K extent of each segment is padded
 // only to 16, so the last chunk of a segment may hold a single BF16 K step
-// (the rest of its 64-byte rows is TMA zero fill)
+// (the rest of its 64-byte rows is TMA zero fill).  kv, ko: chunks of the
+// d and l segments; dp, lp: their padded extents.
 template <int KIND>
-__device__ __forceinline__ int chunk_ksteps(const InstDesc &d, int ch) {
+__device__ __forceinline__ int chunk_ksteps(int kv, int ko, int dp, int lp, int ch) {
     if constexpr (KIND == 1) {
         return 2;  // TF32: 16 elements per chunk, always all data
     } else {
         int kk, kext;
-        if (ch < 2 * d.kv) { kk = ch < d.kv ? ch : ch - d.kv; kext = d.dm.dp; }
-        else { kk = ch - 2 * d.kv; kk = kk < d.ko ? kk : kk - d.ko; kext = d.dm.lp; }
+        if (ch < 2 * kv) { kk = ch < kv ? ch : ch - kv; kext = dp; }
+        else { kk = ch - 2 * kv; kk = kk < ko ? kk : kk - ko; kext = lp; }
         return kext - kk * 32 >= 32 ? 2 : 1;
     }
 }
@@ -373,7 +375,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                 const Item w = decode(wv, it, sc);
                 if (w.diag) continue;
                 const InstDesc &d = *sc.d;
-                const int nch = num_chunks(d), kb = d.kb;
+                // per-item constants in registers: the issue loop reads no memory
+                const int kv = d.kv, ko = d.ko, dp = d.dm.dp, lp = d.dm.lp;
+                const int nch = 2 * kv + 2 * ko, kb = d.kb;
                 const int nvalid = min(BN, d.dm.v - w.n * BN);
                 const int N = (nvalid + 15) / 16 * 16;
                 const uint32_t idesc = idesc_base | ((uint32_t)(N >> 3) << 17);
@@ -402,7 +406,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                         const uint32_t dt = tmem + buf * (uint32_t)BN;
                         const uint32_t sA = sbase + stage * stage_bytes, sAl = sA + A_BYTES;
                         const uint32_t sB = sAl + A_BYTES, sBl = sB + b_plane;
-                        const int nks = chunk_ksteps<KIND>(d, c0 + cb);
+                        const int nks = chunk_ksteps<KIND>(kv, ko, dp, lp, c0 + cb);
                         for (int kk = 0; kk < nks; kk++) {
                             const uint32_t off = kk * 32;
                             tc_mma<KIND>(dt, sdesc(sA + off), sdesc(sBl + off), idesc,
@@ -418,7 +422,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                     int sj = st0;
                     for (int cb = 0; cb < nb; cb++) {
                         const uint32_t sA = sbase + sj * stage_bytes, sB = sA + 2 * A_BYTES;
-                        const int nks = chunk_ksteps<KIND>(d, c0 + cb);
+                        const int nks = chunk_ksteps<KIND>(kv, ko, dp, lp, c0 + cb);
                         for (int kk = 0; kk < nks; kk++) {
                             const uint32_t off = kk * 32;
                             tc_mma<KIND>(dt, sdesc(sA + off), sdesc(sB + off), idesc, 1u);
@@ -471,13 +475,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                 __syncwarp();
                 if (!good) { ok = false; break; }
                 tc_fence_after();
+                // 32 columns per wait, loaded as two 16-column halves (register budget)
 #pragma unroll
-                for (int c8 = 0; c8 < 8; c8++) {
-                    if (c8 < 2 * nld) {  // warp-uniform
-                        uint32_t r[16];
-                        tc_ld16(tmem + lane_off + buf * (uint32_t)BN + (uint32_t)(half * wh + c8 * 16), r);
+                for (int c4 = 0; c4 < 4; c4++) {
+                    if (c4 < nld) {  // warp-uniform
+                        uint32_t r[16], r2[16];
+                        const uint32_t ta = tmem + lane_off + buf * (uint32_t)BN + (uint32_t)(half * wh + c4 * 32);
+                        tc_ld16(ta, r);
+                        tc_ld16(ta + 16, r2);
+                        tc_wait_ld();
 #pragma unroll
-                        for (int j = 0; j < 16; j++) total[c8 * 16 + j] += __uint_as_float(r[j]);
+                        for (int j = 0; j < 16; j++) total[c4 * 32 + j] += __uint_as_float(r[j]);
+#pragma unroll
+                        for (int j = 0; j < 16; j++) total[c4 * 32 + 16 + j] += __uint_as_float(r2[j]);
                     }
                 }
                 tc_fence_before();
