@@ -13,6 +13,14 @@ Two independent implementations:
 * ``bruteforce``: numpy, every ordered (i, j, k) and every (a, b, c), the
   same equations written with einsum and no permutational symmetry; tiny
   sizes only.
+
+RI-MP2 (the paper's second workload, Sec. 2.1):
+
+* ``mp2_energy``: numpy, Eqs. (mp2_energy), (eri_sym_decomp), (e_orb_diff)
+  over every ordered occupied pair (i, j): g = C_i^T C_j with C_i[gamma][a] =
+  C^gamma_ai, then -sum_ab g_ab (2 g_ab - g_ba) / (e_a + e_b - e_i - e_j),
+  split into the Coulomb part -2 sum g^2 / eps and the exchange part
+  +sum g g^T / eps.
 """
 from __future__ import annotations
 
@@ -163,3 +171,23 @@ def bruteforce(inst, with_scale: bool = False, per_triple: bool = False):
         scale = np.sum((abs_tilde(W) + abs_tilde(Y)) * np.abs(W) / np.abs(D))
         return e4, e5, e4 + e5, float(scale)
     return e4, e5, e4 + e5
+
+
+def mp2_energy(inst):
+    """(E_J, E_K, E_MP2) of an RI-MP2 instance (Sec. 2.1): for every ordered
+    occupied pair (i, j) the ERIs g_aibj = sum_gamma C^gamma_ai C^gamma_bj
+    (Eq. eri_sym_decomp, a library matmul) and the energy terms of Eq.
+    (mp2_energy) with eps^{ab}_{ij} = e_a + e_b - e_i - e_j (Eq. e_orb_diff);
+    the exchange integral g_ajbi is g_{b a} of the same pair.  FP64."""
+    eo = np.asarray(inst.eps_occ, dtype=np.float64)
+    ev = np.asarray(inst.eps_vir, dtype=np.float64)
+    C = np.asarray(inst.C, dtype=np.float64)
+    ej = ek = 0.0
+    for i in range(inst.o):
+        Ci = C[:, :, i]
+        for j in range(inst.o):
+            g = Ci.T @ C[:, :, j]
+            eps = ev[:, None] + ev[None, :] - eo[i] - eo[j]
+            ej -= 2.0 * float(np.sum(g * g / eps))
+            ek += float(np.sum(g * g.T / eps))
+    return ej, ek, ej + ek

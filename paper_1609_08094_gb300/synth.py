@@ -235,3 +235,42 @@ def batch_shapes(n: int, seed: int, o_range=(4, 16), v_range=(20, 120)):
         v = v_range[0] + int(uv[idx] * (v_range[1] - v_range[0] + 1))
         out.append((o, v, 3 * (o + v), seed + idx))
     return out
+
+
+@dataclass
+class Mp2Instance:
+    """One synthetic RI-MP2 problem: orbital energies and the fitting
+    coefficients C[gamma][a][i] (numpy on the host or torch tensors)."""
+    o: int
+    v: int
+    naux: int
+    seed: int
+    eps_occ: object
+    eps_vir: object
+    C: object
+
+    def arrays(self):
+        return (self.eps_occ, self.eps_vir, self.C)
+
+    def to(self, device):
+        import torch
+        conv = []
+        for a in self.arrays():
+            t = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(a))
+            conv.append(t.to(device=device, dtype=torch.float64).contiguous())
+        return Mp2Instance(self.o, self.v, self.naux, self.seed, *conv)
+
+
+def make_mp2_instance(o: int, v: int, naux: int | None = None, seed: int = 1) -> Mp2Instance:
+    """The RI-MP2 inputs of the synthetic system of make_instance(o, v, naux,
+    seed): the same orbital energies and, as fitting coefficients, the
+    occupied-virtual block of the same factors, C[gamma][a][i] = B^gamma_{i,o+a}
+    (so that sum_gamma C^gamma_ai C^gamma_bj is that system's (ia|jb))."""
+    if o < 1 or v < 1:
+        raise ValueError("o and v must be >= 1")
+    if naux is None:
+        naux = 3 * (o + v)
+    B = factors(o, v, naux, seed)
+    eo, ev = orbital_energies(o, v, seed)
+    C = np.ascontiguousarray(B[:, :o, o:].transpose(0, 2, 1))
+    return Mp2Instance(o, v, naux, seed, eo, ev, C)
