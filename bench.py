@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--batch-fp64-n", type=int, default=BATCH["fp64_n"])
     ap.add_argument("--wave-mb", type=int, default=0)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-mp2", action="store_true")
     ap.add_argument("--serve-n", type=int, default=SERVE["n"])
     ap.add_argument("--serve-prec", default=SERVE["prec"])
     return ap.parse_args()
@@ -362,6 +363,10 @@ def main():
     if not args.no_serving:
         serving = bench_serving(args, rank, world, stream)
 
+    mp2 = None
+    if not args.no_mp2:
+        mp2 = bench_mp2(args, rank, world, stream)
+
     if rank != 0:
         return
     line = {
@@ -390,6 +395,7 @@ def main():
         "mixed": mixed,
         "batched": batched,
         "serving": serving,
+        "rimp2": mp2,
     }
     print(json.dumps(line), flush=True)
 
@@ -605,6 +611,59 @@ def bench_serving(args, rank, world, stream):
                            "tflops": fl * world / makespan / 1e12, "makespan_s": makespan},
             "waves": st1["waves"] - st0["waves"], "peak_admitted_bytes": st1["peak_bytes"],
             "solo_vs_mixed_identical": f"{same}/{len(sample)}", "generate_s": round(gen_s, 1)}
+
+
+def bench_mp2(args, rank, world, stream):
+    """RI-MP2 (Sec. 2.1) of the same synthetic system as the main workload
+    (its occupied-virtual factors as fitting coefficients), FP64: device time
+    of the fused pair kernel over all i <= j pairs per step, the oracle on the
+    host cores over the whole problem, and their agreement."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1609_08094_gb300 import synth, tcorr
+    o, v, naux, seed = args.o, args.v, args.naux, args.seed
+    t0 = time.time()
+    inst = synth.make_mp2_instance(o, v, naux, seed)
+    gen_s = time.time() - t0
+    dev = inst.to(torch.device("cuda", torch.cuda.current_device()))
+    K, W = args.steps, args.warmup
+    with tcorr.Mp2.from_instance(dev, profile=True, stream=stream) as m:
+        for _ in range(W):
+            m.energy()
+        m.kernel_times(reset=True)
+        barrier(world)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(K):
+            e = m.energy()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = dist_max(ev0.elapsed_time(ev1), world) / K
+        kt = m.kernel_times(reset=True)
+    fl = tcorr.mp2_flops(o, v, naux)
+    kern_ms = kt["gemm"][0] / max(1, kt["gemm"][1])
+    out = {"workload": f"RI-MP2, o={o} v={v} naux={naux} seed={seed} (the main workload's system), FP64, "
+                       "all i <= j pairs per step",
+           "value": fl * world / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms, "steps": K,
+           "pairs_per_s": (o * (o + 1) // 2) * world / (ms * 1e-3), "energy": e, "generate_s": round(gen_s, 1),
+           "roofline": {"bound": "alu", "kernel": "mp2_pair_kernel", "achieved": fl / (kern_ms * 1e-3) / 1e12,
+                        "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": fl / (kern_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                        "note": "achieved counts 2 v^2 naux flops per pair (tiles of 48 compute "
+                                "(ceil(v/48) 48)^2 / v^2 of that plus the diagonal tile pairs twice)"}}
+    if rank == 0 and not args.no_cpu:
+        threads = oracle.max_threads()
+        tc0 = time.time()
+        ref = oracle.mp2_energy(inst)
+        cpu_s = time.time() - tc0
+        out["parity"] = {"rel_err_vs_oracle": abs(e[2] - ref[2]) / abs(ref[2]), "tol": 1e-10,
+                         "oracle_energy": ref}
+        out["cpu_baseline"] = {"value": fl / cpu_s / 1e12, "unit": "TFLOP/s", "cores": threads,
+                               "kind": "oracle", "sample": f"the whole problem (numpy, {cpu_s:.1f} s)"}
+    return out
 
 
 def reference_arm(args):

@@ -282,6 +282,36 @@ const char *tcorr_server_last_error(tcorr_server_t s);
 tcorr_status tcorr_server_destroy(tcorr_server_t s);
 
 /*
+ * RI-MP2 correlation energy (the paper's second workload, Sec. 2.1):
+ *
+ *   E_MP2 = - sum_{ij} sum_{ab} g_aibj (2 g_aibj - g_ajbi) / eps^{ab}_{ij},
+ *   g_aibj = sum_gamma C^gamma_ai C^gamma_bj           (Eqs. mp2_energy, eri_sym_decomp)
+ *   eps^{ab}_{ij} = e_a + e_b - e_i - e_j                (Eq. e_orb_diff)
+ *
+ * evaluated over the occupied pairs i <= j (Eq. tasks_rimp2) in FP64 with the
+ * ERI assembly and the energy fused in one kernel (g is never stored).
+ *
+ *   eps_occ [o], eps_vir [v], C [naux][v][o] = C^gamma_ai (row-major float64;
+ *   device pointers, or host pointers with opts.host_inputs = 1; read only
+ *   during tcorr_mp2_create).
+ *
+ * opts.prec must be TCORR_FP64 (EUNSUPPORTED otherwise); opts.profile times
+ * the kernels (tcorr_mp2_kernel_times: class 1 = the fused pair kernel, 3 =
+ * the final sum).  tcorr_mp2_energy writes e_out[3] = (E_J, E_K, E_MP2) with
+ * E_J = -2 sum g^2/eps (Coulomb) and E_K = +sum g_aibj g_ajbi/eps (exchange).
+ * Errors as for tcorr_create; create failures in tcorr_mp2_last_error(NULL).
+ */
+typedef struct tcorr_mp2_s *tcorr_mp2_t;
+tcorr_status tcorr_mp2_create(tcorr_mp2_t *out, int o, int v, int naux, const double *eps_occ,
+                              const double *eps_vir, const double *C, const tcorr_opts *opts,
+                              void *stream);
+tcorr_status tcorr_mp2_energy(tcorr_mp2_t h, double *e_out);
+tcorr_status tcorr_mp2_kernel_times(tcorr_mp2_t h, double *ms, int64_t *launches, int reset);
+int64_t tcorr_mp2_device_bytes(tcorr_mp2_t h);
+const char *tcorr_mp2_last_error(tcorr_mp2_t h);
+tcorr_status tcorr_mp2_destroy(tcorr_mp2_t h);
+
+/*
  * Allocation-free variant (the paper has no counterpart; it exists for
  * callers that must not allocate device memory: applications whose device
  * memory is owned entirely by their own pool or budget, and latency-sensitive

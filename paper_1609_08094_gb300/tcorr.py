@@ -122,6 +122,20 @@ def load():
         lib.tcorr_server_last_error.argtypes = [sp]
         lib.tcorr_server_destroy.restype = ctypes.c_int
         lib.tcorr_server_destroy.argtypes = [sp]
+        mp = ctypes.c_void_p
+        lib.tcorr_mp2_create.restype = ctypes.c_int
+        lib.tcorr_mp2_create.argtypes = [ctypes.POINTER(mp), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         vp, vp, vp, ctypes.POINTER(Opts), vp]
+        lib.tcorr_mp2_energy.restype = ctypes.c_int
+        lib.tcorr_mp2_energy.argtypes = [mp, dp]
+        lib.tcorr_mp2_kernel_times.restype = ctypes.c_int
+        lib.tcorr_mp2_kernel_times.argtypes = [mp, dp, ctypes.POINTER(i64), ctypes.c_int]
+        lib.tcorr_mp2_device_bytes.restype = i64
+        lib.tcorr_mp2_device_bytes.argtypes = [mp]
+        lib.tcorr_mp2_last_error.restype = ctypes.c_char_p
+        lib.tcorr_mp2_last_error.argtypes = [mp]
+        lib.tcorr_mp2_destroy.restype = ctypes.c_int
+        lib.tcorr_mp2_destroy.argtypes = [mp]
         lib.tcorr_task_energy_noalloc.restype = ctypes.c_int
         lib.tcorr_task_energy_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp,
                                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
@@ -138,6 +152,8 @@ EXPORTS = ("tcorr_create", "tcorr_energy", "tcorr_energy_range", "tcorr_num_task
            "tcorr_server_create", "tcorr_server_submit", "tcorr_server_step", "tcorr_server_poll",
            "tcorr_server_drain", "tcorr_server_stats", "tcorr_server_last_error",
            "tcorr_server_destroy",
+           "tcorr_mp2_create", "tcorr_mp2_energy", "tcorr_mp2_kernel_times", "tcorr_mp2_device_bytes",
+           "tcorr_mp2_last_error", "tcorr_mp2_destroy",
            "tcorr_task_energy_noalloc")
 JOB_STATES = ("queued", "running", "done", "failed")
 SERVER_STATS = ("submitted", "done", "failed", "running", "queued", "bytes", "peak_bytes", "waves")
@@ -462,6 +478,78 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class Mp2:
+    """RI-MP2 correlation energy of one problem (tcorr_mp2_*): eps_occ [o],
+    eps_vir [v], C [naux][v][o] (all CUDA tensors, or all numpy arrays which
+    are copied in).  ``energy()`` returns (E_J, E_K, E_MP2); FP64 only."""
+
+    def __init__(self, o, v, naux, eps_occ, eps_vir, C, profile=False, stream=None, prec="fp64"):
+        lib = load()
+        on_device = bool(getattr(C, "is_cuda", False))
+        shapes = dict(eps_occ=(o,), eps_vir=(v,), C=(naux, v, o))
+        ptrs = []
+        for name, a in (("eps_occ", eps_occ), ("eps_vir", eps_vir), ("C", C)):
+            _shape_check(name, a, shapes[name])
+            ptrs.append(_pointer(name, a, on_device))
+        if isinstance(prec, str):
+            prec = PREC[prec.lower()]
+        opts = Opts(prec=int(prec), host_inputs=0 if on_device else 1, profile=1 if profile else 0)
+        if stream is None and on_device:
+            import torch
+            stream = torch.cuda.current_stream(C.device)
+        sptr = getattr(stream, "cuda_stream", stream) or 0
+        self._stream = stream
+        h = ctypes.c_void_p()
+        st = lib.tcorr_mp2_create(ctypes.byref(h), int(o), int(v), int(naux), *ptrs, ctypes.byref(opts),
+                                  ctypes.c_void_p(sptr))
+        if st != 0:
+            raise TcorrError(st, lib.tcorr_mp2_last_error(None).decode())
+        self._h = h
+        self.o, self.v, self.naux = o, v, naux
+
+    @classmethod
+    def from_instance(cls, inst, **kw):
+        return cls(inst.o, inst.v, inst.naux, *inst.arrays(), **kw)
+
+    def _check(self, st):
+        if st != 0:
+            raise TcorrError(st, load().tcorr_mp2_last_error(self._h).decode())
+
+    def energy(self):
+        e = (ctypes.c_double * 3)()
+        self._check(load().tcorr_mp2_energy(self._h, e))
+        return tuple(e)
+
+    def kernel_times(self, reset: bool = False):
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int64 * 4)()
+        self._check(load().tcorr_mp2_kernel_times(self._h, ms, n, 1 if reset else 0))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tcorr_mp2_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mp2_flops(o: int, v: int, naux: int) -> float:
+    """Algorithmic flops of the ERI assembly over the pairs i <= j: 2 v^2 naux
+    per pair (Sec. 2.1, Eq. tasks_rimp2)."""
+    return 2.0 * v * v * naux * (o * (o + 1) // 2)
 
 
 def task_energy_noalloc(o, v, eps_occ, eps_vir, t1, t2, vvvo, ooov, ovov, ijk, out, stream=None):
