@@ -162,29 +162,43 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const Wave wv) {
 
 
 // Mixed-precision epilogue: the same block-orbit algorithm with 8^3 cubes in
-// FP32, sized for occupancy (about 20 KB of shared memory, 8 CTAs per SM).
+// FP32, sized for occupancy (about 20 KB of shared memory, 48 registers: 5
+// CTAs per SM).  The U loads of a thread are issued first, right after the
+// orbit's block indices are read, and consumed after the Y operands have been
+// staged, so their latency overlaps the staging.
 // The Y operands of the orbit (t1 rows and the three ovov sub-blocks) and
 // the block-relative virtual energies are staged in shared memory.  The
 // denominator of element (x,y,z) is base + d[x] + d[y] + d[z] with
 // base = e_i+e_j+e_k - e_A0 - e_B0 - e_C0 formed in FP64 once per CTA (it is
 // the same for all six cubes of an orbit) and rounded to FP32 once, and
 // d[x] = e_X0 - e_x the FP32 offset from x's block origin.  Element terms
-// are summed in FP32 per thread and warp, and in FP64 (Kahan) across warps.
+// are summed in FP32 per thread, warp and CTA (round to nearest); the orbit
+// partials of a task are summed in FP64 (Kahan) by the task reduction.
 constexpr int F8 = 8;
 constexpr int FP0 = 69, FP1 = 8;    // plane / row pitch of a cube: at most 2-way bank conflicts
 constexpr int FSLOT = F8 * FP0;     // floats per cube slot
+#ifndef EPI_F32_CTAS
+#define EPI_F32_CTAS 5
+#endif
 
-__global__ void __launch_bounds__(NT) epilogue_f32_kernel(const Wave wv) {
+// Position (0, 1, 2) of dimension d of the cube at slot s, for the slots in
+// the order abc, acb, bac, bca, cab, cba, computed in registers.
+__device__ __forceinline__ int perm_pos(int s, int d) {
+    const int p0 = s >> 1;
+    const int lo = p0 == 0 ? 1 : 0, hi = p0 == 2 ? 1 : 2;
+    return d == 0 ? p0 : ((d == 1) == ((s & 1) == 0) ? lo : hi);
+}
+__device__ __forceinline__ int pick3(int a, int b, int c, int k) { return k == 0 ? a : (k == 1 ? b : c); }
+
+__global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wave wv) {
     __shared__ float Ws[6 * FSLOT];
     __shared__ float T1s[3][3][F8];          // [occupied i,j,k][orbit block][local]
     __shared__ float OVs[3][3][3][F8 * F8];  // [(jk),(ik),(ij)][block][block][8x8]
     __shared__ float Dls[3][F8];             // [orbit block][local] block-relative energies
     __shared__ float base_s;
     __shared__ int comp[6][6];
-    __shared__ int pos[6][3];                // orbit position (0,1,2 = A,B,C) of each cube dim
     __shared__ int distinct[6];
-    __shared__ int ob[3];
-    __shared__ double red[NT / 32][2];
+    __shared__ float red[NT / 32][2];
 
     const int64_t item = blockIdx.x;
     const Seg sg = wv.segs[seg_find(wv.segs, wv.nseg, item, [](const Seg &x) { return x.epi0; })];
@@ -200,60 +214,14 @@ __global__ void __launch_bounds__(NT) epilogue_f32_kernel(const Wave wv) {
         if (tid == 0) { out[0] = 0.0; out[1] = 0.0; }
         return;
     }
-    const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-    if (tid < 36) {
-        const int pi = tid / 6, q = tid % 6;
-        const int t0 = P[pi][P[q][0]], t1v = P[pi][P[q][1]], t2v = P[pi][P[q][2]];
-        int sig = 0;
-        for (int s = 0; s < 6; s++)
-            if (P[s][0] == t0 && P[s][1] == t1v && P[s][2] == t2v) sig = s;
-        comp[pi][q] = sig;
-    }
-    if (tid < 3) ob[tid] = p.orbits[3 * orb + tid];
-    if (tid >= 64 && tid < 70) {
-        const int s = tid - 64;
-        pos[s][0] = P[s][0];
-        pos[s][1] = P[s][1];
-        pos[s][2] = P[s][2];
-    }
-    __syncthreads();
-    if (tid < 6) {
-        int d = 1;
-        for (int s = 0; s < tid; s++)
-            if (ob[P[s][0]] == ob[P[tid][0]] && ob[P[s][1]] == ob[P[tid][1]] && ob[P[s][2]] == ob[P[tid][2]]) d = 0;
-        distinct[tid] = d;
-    }
-    if (tid == 96) {
-        const double eijk = p.eps_o[ti] + p.eps_o[tj] + p.eps_o[tkk];
-        base_s = (float)(eijk - p.eps_v[ob[0] * F8] - p.eps_v[ob[1] * F8] - p.eps_v[ob[2] * F8]);
-    }
-    // stage t1, ovov sub-blocks and block-relative energies
-    const float *t1 = static_cast<const float *>(p.t1);
-    const float *ov = static_cast<const float *>(p.ovov);
-    for (int e = tid; e < 3 * 3 * F8; e += NT) {
-        const int oc = e / (3 * F8), b = (e / F8) % 3, m = e % F8;
-        const int x = ob[b] * F8 + m;
-        const int occ = oc == 0 ? ti : (oc == 1 ? tj : tkk);
-        T1s[oc][b][m] = x < v ? t1[occ * v + x] : 0.f;
-    }
-    for (int e = tid; e < 3 * F8; e += NT) {
-        const int b = e / F8, m = e % F8, x = ob[b] * F8 + m;
-        Dls[b][m] = x < v ? p.dev_f[x] : 0.f;
-    }
-    // slices: 0 = (j y | k z), 1 = (i x | k z), 2 = (i x | j y)
-    for (int e = tid; e < 3 * 9 * F8 * F8; e += NT) {
-        const int sl = e / (9 * 64), bb = (e / 64) % 9, m = (e / 8) % 8, n = e % 8;
-        const int ba = bb / 3, bc = bb % 3;
-        const int r = ob[ba] * F8 + m, c = ob[bc] * F8 + n;
-        const int first = sl == 0 ? tj : ti, second = sl == 2 ? tj : tkk;
-        float val = 0.f;
-        if (r < v && c < v) val = ov[(((int64_t)first * v + r) * o + second) * v + c];
-        OVs[sl][ba][bc][m * F8 + n] = val;
-    }
+    // every thread reads the orbit's blocks itself (no shared-memory round trip),
+    // so the U loads below can be issued before any barrier
+    const int ob0 = p.orbits[3 * orb], ob1 = p.orbits[3 * orb + 1], ob2 = p.orbits[3 * orb + 2];
+#define OBP(s, d) pick3(ob0, ob1, ob2, perm_pos((s), (d)))
 
     // W[x][y][z] = S0[x][y][z] + S1[x][y][z] + S2[z][x][y]: slots 0 and 1 read
-    // along z, slot 2 along y (all rows contiguous); all float4 loads of a
-    // thread are issued before any use.
+    // along z, slot 2 along y (all rows contiguous); the loads are issued first
+    // and consumed after the Y operands have been staged.
     const float *S0 = static_cast<const float *>(wv.U) + sg.u_off + (int64_t)(tb * 3 + 0) * v2 * vc;
     const int64_t gs = v2 * vc;
     float4 ra[3], rb[3], rc[3];
@@ -261,26 +229,68 @@ __global__ void __launch_bounds__(NT) epilogue_f32_kernel(const Wave wv) {
     for (int it = 0; it < 3; it++) {
         const int idx = tid + it * NT;            // 6 slots x 64 rows x 2 halves = 768
         const int s = idx >> 7, row = (idx >> 1) & 63, hf = idx & 1;
-        // slots 0,1: row (x, y), 4 values of z
-        const int x = ob[pos[s][0]] * F8 + (row >> 3), y = ob[pos[s][1]] * F8 + (row & 7);
-        const int z0 = ob[pos[s][2]] * F8 + hf * 4;
+        const int x = OBP(s, 0) * F8 + (row >> 3), y = OBP(s, 1) * F8 + (row & 7);
+        const int z0 = OBP(s, 2) * F8 + hf * 4;
         ra[it] = rb[it] = rc[it] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (x < v && y < v && z0 < v) {
             const float4 *q = reinterpret_cast<const float4 *>(S0 + ((int64_t)x * v + y) * vc + z0);
             ra[it] = __ldg(q);
             rb[it] = __ldg(q + gs / 4);
         }
-        // slot 2: row (z, x), 4 values of y
-        const int z = ob[pos[s][2]] * F8 + (row >> 3), x2 = ob[pos[s][0]] * F8 + (row & 7);
-        const int y0 = ob[pos[s][1]] * F8 + hf * 4;
+        const int z = OBP(s, 2) * F8 + (row >> 3), x2 = OBP(s, 0) * F8 + (row & 7);
+        const int y0 = OBP(s, 1) * F8 + hf * 4;
         if (z < v && x2 < v && y0 < v)
             rc[it] = __ldg(reinterpret_cast<const float4 *>(S0 + 2 * gs + ((int64_t)z * v + x2) * vc + y0));
     }
+
+    if (tid < 36) {  // comp[pi][q]: the slot of permutation pi composed with q
+        const int pi = tid / 6, q = tid % 6;
+        const int t0 = perm_pos(pi, perm_pos(q, 0)), t1v = perm_pos(pi, perm_pos(q, 1));
+        int sig = 0;
+        for (int s = 0; s < 6; s++)
+            if (perm_pos(s, 0) == t0 && perm_pos(s, 1) == t1v) sig = s;
+        comp[pi][q] = sig;
+    }
+    if (tid >= 64 && tid < 70) {
+        const int t = tid - 64;
+        int d = 1;
+        for (int s = 0; s < t; s++)
+            if (OBP(s, 0) == OBP(t, 0) && OBP(s, 1) == OBP(t, 1) && OBP(s, 2) == OBP(t, 2)) d = 0;
+        distinct[t] = d;
+    }
+    if (tid == 96) {
+        const double eijk = p.eps_o[ti] + p.eps_o[tj] + p.eps_o[tkk];
+        base_s = (float)(eijk - p.eps_v[ob0 * F8] - p.eps_v[ob1 * F8] - p.eps_v[ob2 * F8]);
+    }
+    // stage t1, ovov sub-blocks and block-relative energies
+    const float *t1 = static_cast<const float *>(p.t1);
+    const float *ov = static_cast<const float *>(p.ovov);
+    for (int e = tid; e < 3 * 3 * F8; e += NT) {
+        const int oc = e / (3 * F8), b = (e / F8) % 3, m = e % F8;
+        const int x = pick3(ob0, ob1, ob2, b) * F8 + m;
+        const int occ = oc == 0 ? ti : (oc == 1 ? tj : tkk);
+        T1s[oc][b][m] = x < v ? t1[occ * v + x] : 0.f;
+    }
+    for (int e = tid; e < 3 * F8; e += NT) {
+        const int b = e / F8, m = e % F8, x = pick3(ob0, ob1, ob2, b) * F8 + m;
+        Dls[b][m] = x < v ? p.dev_f[x] : 0.f;
+    }
+    // slices: 0 = (j y | k z), 1 = (i x | k z), 2 = (i x | j y)
+    for (int e = tid; e < 3 * 9 * F8 * F8; e += NT) {
+        const int sl = e / (9 * 64), bb = (e / 64) % 9, m = (e / 8) % 8, n = e % 8;
+        const int ba = bb / 3, bc = bb % 3;
+        const int r = pick3(ob0, ob1, ob2, ba) * F8 + m, c = pick3(ob0, ob1, ob2, bc) * F8 + n;
+        const int first = sl == 0 ? tj : ti, second = sl == 2 ? tj : tkk;
+        float val = 0.f;
+        if (r < v && c < v) val = ov[(((int64_t)first * v + r) * o + second) * v + c];
+        OVs[sl][ba][bc][m * F8 + n] = val;
+    }
+
 #pragma unroll
     for (int it = 0; it < 3; it++) {
         const int idx = tid + it * NT;
         const int s = idx >> 7, row = (idx >> 1) & 63, hf = idx & 1;
-        const int z0 = ob[pos[s][2]] * F8 + hf * 4;
+        const int z0 = OBP(s, 2) * F8 + hf * 4;
         float *wrow = Ws + s * FSLOT + (row >> 3) * FP0 + (row & 7) * FP1 + hf * 4;
         const float w[4] = {ra[it].x + rb[it].x, ra[it].y + rb[it].y, ra[it].z + rb[it].z, ra[it].w + rb[it].w};
 #pragma unroll
@@ -292,7 +302,7 @@ __global__ void __launch_bounds__(NT) epilogue_f32_kernel(const Wave wv) {
         const int idx = tid + it * NT;
         const int s = idx >> 7, row = (idx >> 1) & 63, hf = idx & 1;
         const int lz = row >> 3, lx = row & 7;
-        const int y0 = ob[pos[s][1]] * F8 + hf * 4;
+        const int y0 = OBP(s, 1) * F8 + hf * 4;
         const float w[4] = {rc[it].x, rc[it].y, rc[it].z, rc[it].w};
 #pragma unroll
         for (int m = 0; m < 4; m++)
@@ -302,14 +312,14 @@ __global__ void __launch_bounds__(NT) epilogue_f32_kernel(const Wave wv) {
 
     const float base = base_s;
     float a4 = 0.f, a5 = 0.f;
-    if (ob[0] < ob[1] && ob[1] < ob[2]) {
+    if (ob0 < ob1 && ob1 < ob2) {
         // Distinct blocks: each thread takes element orbits, the six orderings
         // of one (a,b,c) with a in A, b in B, c in C.  Slot q holds the element
         // with indices ordered as q (slots 0..5 = abc, acb, bac, bca, cab, cba);
         // even slots 0,3,4, odd slots 1,2,5.  With E and O the sums of W over
         // the even and odd slots, Z at slot q is 6 w_q + 2E - 4O (q even) or
         // 6 w_q + 2O - 4E (q odd), and all six share one denominator.
-        const int A0 = ob[0] * F8, B0 = ob[1] * F8, C0 = ob[2] * F8;
+        const int A0 = ob0 * F8, B0 = ob1 * F8, C0 = ob2 * F8;
         for (int l = tid; l < 512; l += NT) {
             const int la = l >> 6, lb = (l >> 3) & 7, lc = l & 7;
             if (A0 + la >= v || B0 + lb >= v || C0 + lc >= v) continue;
@@ -352,13 +362,14 @@ __global__ void __launch_bounds__(NT) epilogue_f32_kernel(const Wave wv) {
         // blocks repeat: element by element over the distinct cube slots
         for (int s = 0; s < 6; s++) {
             if (!distinct[s]) continue;
-            const int p0 = pos[s][0], p1 = pos[s][1], p2 = pos[s][2];
+            const int p0 = perm_pos(s, 0), p1 = perm_pos(s, 1), p2 = perm_pos(s, 2);
             const float *W0 = Ws + comp[s][0] * FSLOT, *W1 = Ws + comp[s][1] * FSLOT;
             const float *W2 = Ws + comp[s][2] * FSLOT, *W3 = Ws + comp[s][3] * FSLOT;
             const float *W4 = Ws + comp[s][4] * FSLOT, *W5 = Ws + comp[s][5] * FSLOT;
             for (int l = tid; l < 512; l += NT) {
                 const int l0 = l >> 6, l1 = (l >> 3) & 7, l2 = l & 7;
-                const int x = ob[p0] * F8 + l0, y = ob[p1] * F8 + l1, z = ob[p2] * F8 + l2;
+                const int x = pick3(ob0, ob1, ob2, p0) * F8 + l0, y = pick3(ob0, ob1, ob2, p1) * F8 + l1,
+                          z = pick3(ob0, ob1, ob2, p2) * F8 + l2;
                 if (x >= v || y >= v || z >= v) continue;
                 const float w0 = W0[l0 * FP0 + l1 * FP1 + l2];
                 // Z = 8 W(abc) - 4 (W(acb) + W(bac) + W(cba)) + 2 (W(bca) + W(cab))
@@ -379,15 +390,23 @@ __global__ void __launch_bounds__(NT) epilogue_f32_kernel(const Wave wv) {
         a4 += __shfl_xor_sync(0xffffffffu, a4, off);
         a5 += __shfl_xor_sync(0xffffffffu, a5, off);
     }
-    if ((tid & 31) == 0) { red[tid >> 5][0] = (double)a4; red[tid >> 5][1] = (double)a5; }
+    // cross-warp sum in FP32 (8 terms, round to nearest); the orbit partials are
+    // summed in FP64 (Kahan) per task
+    if ((tid & 31) == 0) { red[tid >> 5][0] = a4; red[tid >> 5][1] = a5; }
     __syncthreads();
-    if (tid == 0) {
-        double t4 = 0.0, k4 = 0.0, t5 = 0.0, k5 = 0.0;
-        for (int w = 0; w < NT / 32; w++) { kahan_add(t4, k4, red[w][0]); kahan_add(t5, k5, red[w][1]); }
-        out[0] = t4 - k4;
-        out[1] = t5 - k5;
+    if (tid < 32) {
+        float b4 = tid < NT / 32 ? red[tid][0] : 0.f, b5 = tid < NT / 32 ? red[tid][1] : 0.f;
+        for (int off = 4; off > 0; off >>= 1) {
+            b4 += __shfl_xor_sync(0xffffffffu, b4, off);
+            b5 += __shfl_xor_sync(0xffffffffu, b5, off);
+        }
+        if (tid == 0) {
+            out[0] = (double)b4;
+            out[1] = (double)b5;
+        }
     }
 }
+#undef OBP
 
 // One CTA per task of the wave: Kahan sum of its orbit partials, times m/6.
 __global__ void __launch_bounds__(NT) task_reduce_kernel(const Wave wv) {
