@@ -11,7 +11,8 @@
 // computes both G = C_i[A] C_j[B]^T (= g on A x B) and H = C_j[A] C_i[B]^T
 // (= g on B x A, transposed), so every thread holds g_ab and g_ba for the same
 // (a, b) and the energy terms are formed in registers: g never reaches
-// memory.  Over A x B and B x A together the Coulomb part is 2 (G^2 + H^2)/eps
+// memory.  On a diagonal tile pair H = G^T is taken from G through shared
+// memory instead of being computed.  Over A x B and B x A together the Coulomb part is 2 (G^2 + H^2)/eps
 // and the exchange part 2 G H / eps; a diagonal tile pair (A = B) covers its
 // block once, G^2 and G H.  The GEMM is a register-tiled DFMA loop (3 x 3
 // outputs of each of G and H per thread, K = naux in chunks of 8 staged
@@ -99,32 +100,61 @@ __global__ void __launch_bounds__(MNT, 2) mp2_pair_kernel(const Mp2Args p) {
         for (int c = 0; c < 3; c++) G[r][c] = H[r][c] = 0.0;
 
     const int nch = kp / MK;
+    const bool diag = (A == B);  // H = G^T on a diagonal tile pair: computed from G below
     fetch(0);
     stash(0);
     __syncthreads();
     for (int ch = 0; ch < nch; ch++) {
         const int buf = ch & 1;
         if (ch + 1 < nch) fetch((ch + 1) * MK);
+        if (!diag) {
 #pragma unroll
-        for (int k = 0; k < MK; k++) {
-            double ai[3], bj[3], aj[3], bi[3];
+            for (int k = 0; k < MK; k++) {
+                double ai[3], bj[3], aj[3], bi[3];
 #pragma unroll
-            for (int r = 0; r < 3; r++) {
-                ai[r] = sm[buf][0][k][ta + 16 * r];
-                aj[r] = sm[buf][2][k][ta + 16 * r];
-                bj[r] = sm[buf][1][k][tb + 16 * r];
-                bi[r] = sm[buf][3][k][tb + 16 * r];
-            }
-#pragma unroll
-            for (int r = 0; r < 3; r++)
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    G[r][c] = fma(ai[r], bj[c], G[r][c]);
-                    H[r][c] = fma(aj[r], bi[c], H[r][c]);
+                for (int r = 0; r < 3; r++) {
+                    ai[r] = sm[buf][0][k][ta + 16 * r];
+                    aj[r] = sm[buf][2][k][ta + 16 * r];
+                    bj[r] = sm[buf][1][k][tb + 16 * r];
+                    bi[r] = sm[buf][3][k][tb + 16 * r];
                 }
+#pragma unroll
+                for (int r = 0; r < 3; r++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        G[r][c] = fma(ai[r], bj[c], G[r][c]);
+                        H[r][c] = fma(aj[r], bi[c], H[r][c]);
+                    }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < MK; k++) {
+                double ai[3], bj[3];
+#pragma unroll
+                for (int r = 0; r < 3; r++) {
+                    ai[r] = sm[buf][0][k][ta + 16 * r];
+                    bj[r] = sm[buf][1][k][tb + 16 * r];
+                }
+#pragma unroll
+                for (int r = 0; r < 3; r++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++) G[r][c] = fma(ai[r], bj[c], G[r][c]);
+            }
         }
         if (ch + 1 < nch) stash(buf ^ 1);
         __syncthreads();
+    }
+    if (diag) {  // H[a][b] = g[b][a] = G at (b, a), through shared memory (the K loop is done with it)
+        double *Gs = &sm[0][0][0][0];  // 48 x 48 doubles (2 x 4 x 8 x 48 available)
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) Gs[(ta + 16 * r) * MT + tb + 16 * c] = G[r][c];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) H[r][c] = Gs[(tb + 16 * c) * MT + ta + 16 * r];
     }
 
     // energy terms of this thread's (a, b)
