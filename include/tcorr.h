@@ -51,7 +51,12 @@ typedef enum {
     TCORR_TF32X3 = 1,  /* W contractions on tcgen05 tensor cores, TF32 hi+lo split, 3 products,
                           FP32 accumulation; denominators and energy sum in FP64 (Sec. 3 mixed
                           precision, re-designed) */
-    TCORR_BF16X3 = 2   /* as TF32X3 with BF16 hi+lo operands */
+    TCORR_BF16X3 = 2,  /* as TF32X3 with BF16 hi+lo operands */
+    TCORR_FP64_OZ = 3  /* FP64-accurate W contractions on the BF16 tensor cores: each operand split
+                          into 5 signed 7-bit slices under one power-of-two scale per operand side
+                          (Ozaki scheme), slice products summed exactly in FP32 per 32-element K
+                          chunk and in int64 across chunks, U rounded once to FP64; FP64 energy
+                          epilogue.  sm_103 only; device or host inputs; batch and server too */
 } tcorr_precision;
 
 typedef struct {

@@ -33,7 +33,19 @@ __device__ __forceinline__ void kahan_add(double &s, double &c, double x) {
     s = t;
 }
 
-// FP64 epilogue (the generic per-element form); TE: cube edge.
+// Position (0, 1, 2) of dimension d of the cube at slot s, for the slots in
+// the order abc, acb, bac, bca, cab, cba, computed in registers.
+__device__ __forceinline__ int perm_pos(int s, int d) {
+    const int p0 = s >> 1;
+    const int lo = p0 == 0 ? 1 : 0, hi = p0 == 2 ? 1 : 2;
+    return d == 0 ? p0 : ((d == 1) == ((s & 1) == 0) ? lo : hi);
+}
+__device__ __forceinline__ int pick3(int a, int b, int c, int k) { return k == 0 ? a : (k == 1 ? b : c); }
+
+// FP64 epilogue; TE: cube edge.  Orbits of three distinct blocks take the
+// element-orbit form (the six orderings of one (a,b,c) share one denominator
+// and the E/O expansion of Z, as in the mixed epilogue), orbits with repeated
+// blocks the generic per-element form.
 template <typename UT, typename CT, int TE>
 __global__ void __launch_bounds__(NT) epilogue_kernel(const Wave wv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -119,22 +131,68 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const Wave wv) {
     const int64_t ovs = (int64_t)o * v;
 
     double s4 = 0.0, c4 = 0.0, s5 = 0.0, c5 = 0.0;
+    if (blk[0][0] < blk[0][1] && blk[0][1] < blk[0][2]) {
+        // distinct blocks A < B < C: element orbits; slot q holds the element
+        // with indices ordered as q (abc, acb, bac, bca, cab, cba); even slots
+        // 0, 3, 4, odd 1, 2, 5; Z_q = 6 w_q + 2E - 4O (even) or 6 w_q + 2O - 4E (odd)
+        const int A0 = blk[0][0] * TE, B0 = blk[0][1] * TE, C0 = blk[0][2] * TE;
+        CT a4 = CT(0), a5 = CT(0);
+        for (int l = tid; l < NE; l += NT) {
+            const int la = l / (TE * TE), lb = (l / TE) % TE, lc = l % TE;
+            const int a = A0 + la, b = B0 + lb, c = C0 + lc;
+            if (a >= v || b >= v || c >= v) continue;
+            const CT w0 = Ws[0 * CUBE + (la * TE + lb) * TP + lc];
+            const CT w1 = Ws[1 * CUBE + (la * TE + lc) * TP + lb];
+            const CT w2 = Ws[2 * CUBE + (lb * TE + la) * TP + lc];
+            const CT w3 = Ws[3 * CUBE + (lb * TE + lc) * TP + la];
+            const CT w4 = Ws[4 * CUBE + (lc * TE + la) * TP + lb];
+            const CT w5 = Ws[5 * CUBE + (lc * TE + lb) * TP + la];
+            const CT tia = t1[ti * v + a], tib = t1[ti * v + b], tic = t1[ti * v + c];
+            const CT tja = t1[tj * v + a], tjb = t1[tj * v + b], tjc = t1[tj * v + c];
+            const CT tka = t1[tkk * v + a], tkb = t1[tkk * v + b], tkc = t1[tkk * v + c];
+            // (j u | k w), (i u | k w), (i u | j w) over ordered pairs of {a, b, c}
+            const CT jk_bc = ov_jk[b * ovs + c], jk_cb = ov_jk[c * ovs + b], jk_ac = ov_jk[a * ovs + c];
+            const CT jk_ca = ov_jk[c * ovs + a], jk_ab = ov_jk[a * ovs + b], jk_ba = ov_jk[b * ovs + a];
+            const CT ik_bc = ov_ik[b * ovs + c], ik_cb = ov_ik[c * ovs + b], ik_ac = ov_ik[a * ovs + c];
+            const CT ik_ca = ov_ik[c * ovs + a], ik_ab = ov_ik[a * ovs + b], ik_ba = ov_ik[b * ovs + a];
+            const CT ij_bc = ov_ij[b * ovs + c], ij_cb = ov_ij[c * ovs + b], ij_ac = ov_ij[a * ovs + c];
+            const CT ij_ca = ov_ij[c * ovs + a], ij_ab = ov_ij[a * ovs + b], ij_ba = ov_ij[b * ovs + a];
+            // Y at each ordering q of (a,b,c): t^{q0}_i (j q1|k q2) + t^{q1}_j (i q0|k q2) + t^{q2}_k (i q0|j q1)
+            const CT y0 = tia * jk_bc + tjb * ik_ac + tkc * ij_ab;
+            const CT y1 = tia * jk_cb + tjc * ik_ab + tkb * ij_ac;
+            const CT y2 = tib * jk_ac + tja * ik_bc + tkc * ij_ba;
+            const CT y3 = tib * jk_ca + tjc * ik_ba + tka * ij_bc;
+            const CT y4 = tic * jk_ab + tja * ik_cb + tkb * ij_ca;
+            const CT y5 = tic * jk_ba + tjb * ik_ca + tka * ij_cb;
+            const CT E = w0 + w3 + w4, O = w1 + w2 + w5;
+            const CT ww = w0 * w0 + w1 * w1 + w2 * w2 + w3 * w3 + w4 * w4 + w5 * w5;
+            const CT wy = w0 * y0 + w1 * y1 + w2 * y2 + w3 * y3 + w4 * y4 + w5 * y5;
+            const CT q4 = CT(6) * ww + CT(2) * (E * E + O * O) - CT(8) * E * O;
+            const CT q5 = CT(6) * wy + (CT(2) * E - CT(4) * O) * (y0 + y3 + y4) + (CT(2) * O - CT(4) * E) * (y1 + y2 + y5);
+            const CT r = CT(1) / (eijk - p.eps_v[a] - p.eps_v[b] - p.eps_v[c]);
+            a4 += q4 * r;
+            a5 += q5 * r;
+        }
+        kahan_add(s4, c4, double(a4));
+        kahan_add(s5, c5, double(a5));
+    } else
     for (int s = 0; s < 6; s++) {
         if (!distinct[s]) continue;
         CT a4 = CT(0), a5 = CT(0);
         const int X0 = blk[s][0] * TE, Y0 = blk[s][1] * TE, Z0 = blk[s][2] * TE;
         for (int l = tid; l < NE; l += NT) {
-            const int lv[3] = {l / (TE * TE), (l / TE) % TE, l % TE};
-            const int x = X0 + lv[0], y = Y0 + lv[1], z = Z0 + lv[2];
+            const int lv0 = l / (TE * TE), lv1 = (l / TE) % TE, lv2 = l % TE;
+            const int x = X0 + lv0, y = Y0 + lv1, z = Z0 + lv2;
             if (x >= v || y >= v || z >= v) continue;
             CT zv = CT(0);
 #pragma unroll
             for (int q = 0; q < 6; q++) {
                 const int sg = comp[s][q];
-                const int m0 = lv[P[q][0]], m1 = lv[P[q][1]], m2 = lv[P[q][2]];
+                const int m0 = pick3(lv0, lv1, lv2, perm_pos(q, 0)), m1 = pick3(lv0, lv1, lv2, perm_pos(q, 1)),
+                          m2 = pick3(lv0, lv1, lv2, perm_pos(q, 2));
                 zv += coef[q] * Ws[sg * CUBE + (m0 * TE + m1) * TP + m2];
             }
-            const CT w0 = Ws[s * CUBE + (lv[0] * TE + lv[1]) * TP + lv[2]];
+            const CT w0 = Ws[s * CUBE + (lv0 * TE + lv1) * TP + lv2];
             const CT yv = t1[ti * v + x] * ov_jk[y * ovs + z] + t1[tj * v + y] * ov_ik[x * ovs + z] +
                           t1[tkk * v + z] * ov_ij[x * ovs + y];
             const CT dn = eijk - p.eps_v[x] - p.eps_v[y] - p.eps_v[z];
@@ -180,15 +238,6 @@ constexpr int FSLOT = F8 * FP0;     // floats per cube slot
 #ifndef EPI_F32_CTAS
 #define EPI_F32_CTAS 5
 #endif
-
-// Position (0, 1, 2) of dimension d of the cube at slot s, for the slots in
-// the order abc, acb, bac, bca, cab, cba, computed in registers.
-__device__ __forceinline__ int perm_pos(int s, int d) {
-    const int p0 = s >> 1;
-    const int lo = p0 == 0 ? 1 : 0, hi = p0 == 2 ? 1 : 2;
-    return d == 0 ? p0 : ((d == 1) == ((s & 1) == 0) ? lo : hi);
-}
-__device__ __forceinline__ int pick3(int a, int b, int c, int k) { return k == 0 ? a : (k == 1 ? b : c); }
 
 __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wave wv) {
     __shared__ float Ws[6 * FSLOT];

@@ -86,14 +86,90 @@ void resolve_timers(Exec &ex) {
     ex.pending.swap(keep);
 }
 
-int elem_kind(int prec) { return prec == TCORR_FP64 ? 0 : (prec == TCORR_TF32X3 ? 1 : 2); }
+int elem_kind(int prec) { return prec == TCORR_FP64 ? 0 : (prec == TCORR_TF32X3 ? 1 : (prec == TCORR_BF16X3 ? 2 : 3)); }
+bool is_split(int prec) { return prec == TCORR_TF32X3 || prec == TCORR_BF16X3; }
+bool fp64_epilogue(int prec) { return prec == TCORR_FP64 || prec == TCORR_FP64_OZ; }
 size_t elem_bytes(int prec) { return prec == TCORR_FP64 ? 8 : (prec == TCORR_TF32X3 ? 4 : 2); }
-size_t u_elem_bytes(int prec) { return prec == TCORR_FP64 ? 8 : 4; }
+size_t u_elem_bytes(int prec) { return fp64_epilogue(prec) ? 8 : 4; }
+// operand planes per element: 1 (FP64), 2 (hi + lo), or the FP64-emulation slices
+static size_t operand_planes(int prec) { return prec == TCORR_FP64 ? 1 : (is_split(prec) ? 2 : (size_t)oz_slices()); }
+
+// FP64 emulation: the operands as oz_slices() BF16 slice planes under one
+// power-of-two scale per operand side (exponents computed on the device from
+// max |vvvo|, |t2|, |ooov|, so nothing here waits for the device).
+static void build_operands_oz(Exec &ex, Problem &pb, const double *t2, const double *vvvo, const double *ooov,
+                              bool host) {
+    const int o = pb.dm.o, v = pb.dm.v, dp = pb.dm.dp, lp = pb.dm.lp;
+    const int64_t v2 = (int64_t)v * v;
+    const size_t S = (size_t)oz_slices();
+    const size_t nG = (size_t)o * v2 * dp, nT2K = (size_t)o * v2 * lp;
+    const size_t nT2R = (size_t)o * o * v * dp, nAoN = (size_t)o * o * v * lp;
+    Operands &op = pb.op;
+    dalloc(ex, op.G, nG * 2 * S);
+    dalloc(ex, op.T2K, nT2K * 2 * S);
+    dalloc(ex, op.T2R, nT2R * 2 * S);
+    dalloc(ex, op.AoN, nAoN * 2 * S);
+    dalloc(ex, pb.oz_max, 3 * sizeof(unsigned long long));
+    dalloc(ex, pb.oz_e, 2 * sizeof(int));
+    Timer tm(ex, KC_PREP);
+    CK(cudaMemsetAsync(pb.oz_max, 0, 3 * sizeof(unsigned long long), ex.stream));
+    CK(cudaMemsetAsync(op.G, 0, nG * 2 * S, ex.stream));
+    double *tmp_t2 = nullptr, *tmp_oo = nullptr;
+    const double *dt2 = device_view(ex, t2, (size_t)o * o * v2, host, tmp_t2);
+    const double *doo = device_view(ex, ooov, (size_t)o * o * o * v, host, tmp_oo);
+    const size_t row = (size_t)v2 * o;  // doubles per d row of vvvo
+    if (!host) {
+        CK(launch_maxabs(vvvo, (int64_t)(row * v), pb.oz_max, ex.stream));
+    } else {
+        double m = 0.0;
+        for (size_t k = 0; k < row * v; k++) m = std::max(m, std::fabs(vvvo[k]));
+        CK(launch_seed_max(pb.oz_max, m, ex.stream));
+    }
+    CK(launch_maxabs(dt2, (int64_t)o * o * v2, pb.oz_max + 1, ex.stream));
+    CK(launch_maxabs(doo, (int64_t)o * o * o * v, pb.oz_max + 2, ex.stream));
+    CK(launch_oz_exponents(pb.oz_max, pb.oz_e, ex.stream));
+    const int *eA = pb.oz_e, *eB = pb.oz_e + 1;
+    // G[p][q][xy][d] = slices of vvvo[d][xy][q]
+    if (!host) {
+        CK(launch_slice_pad(vvvo, op.G, v2, v, v, o, o, (int64_t)row, 1, dp, (int64_t)v2 * dp, (int64_t)nG, eA, 1.0,
+                            ex.stream));
+    } else {
+        size_t rows_per = (size_t)((512ull << 20) / (row * sizeof(double)));
+        if (rows_per < 1) rows_per = 1;
+        if (rows_per > (size_t)v) rows_per = v;
+        double *stage = nullptr;
+        dalloc(ex, stage, rows_per * row * sizeof(double));
+        for (int d0 = 0; d0 < v; d0 += (int)rows_per) {
+            const int nr = (int)((size_t)(v - d0) < rows_per ? (size_t)(v - d0) : rows_per);
+            CK(cudaMemcpyAsync(stage, vvvo + (size_t)d0 * row, nr * row * sizeof(double), cudaMemcpyHostToDevice,
+                               ex.stream));
+            char *g = static_cast<char *>(op.G) + (size_t)d0 * 2;
+            CK(launch_slice_pad(stage, g, v2, nr, nr, o, o, (int64_t)row, 1, dp, (int64_t)v2 * dp, (int64_t)nG, eA,
+                                1.0, ex.stream));
+        }
+        free_tmp(ex, stage, rows_per * row);
+    }
+    // T2K[p][q][xy][l] = slices of t2[q][l][xy]; T2R[p][spa][d] = slices of t2[spa][d]
+    CK(launch_slice_pad(dt2, op.T2K, o, o, lp, v2, (int64_t)o * v2, v2, 1, (int64_t)v2 * lp, lp, (int64_t)nT2K, eA,
+                        1.0, ex.stream));
+    CK(launch_slice_pad(dt2, op.T2R, (int64_t)o * o * v, v, dp, 1, v, 1, 0, dp, 0, (int64_t)nT2R, eB, 1.0,
+                        ex.stream));
+    // AoN[p][qsa][l] = slices of -ooov[l][qsa]
+    CK(launch_slice_pad(doo, op.AoN, 1, o, lp, (int64_t)o * o * v, 0, (int64_t)o * o * v, 1, 0, lp, (int64_t)nAoN,
+                        eB, -1.0, ex.stream));
+    tm.stop();
+    free_tmp(ex, tmp_t2, (size_t)o * o * v2);
+    free_tmp(ex, tmp_oo, (size_t)o * o * o * v);
+}
 
 Dims make_dims(int o, int v) { return Dims{o, v, round_up(v, KPAD), round_up(o, KPAD), round_up(v, UPAD)}; }
 
 void build_operands(Exec &ex, Problem &pb, const double *t2, const double *vvvo, const double *ooov,
                     bool host) {
+    if (ex.prec == TCORR_FP64_OZ) {
+        build_operands_oz(ex, pb, t2, vvvo, ooov, host);
+        return;
+    }
     const int o = pb.dm.o, v = pb.dm.v, dp = pb.dm.dp, lp = pb.dm.lp;
     const int64_t v2 = (int64_t)v * v;
     const int kind = elem_kind(ex.prec);
@@ -163,7 +239,7 @@ void build_epilogue_inputs(Exec &ex, Problem &pb, const double *eps_occ, const d
     const cudaMemcpyKind kd = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     CK(cudaMemcpyAsync(pb.eps_o, eps_occ, o * sizeof(double), kd, ex.stream));
     CK(cudaMemcpyAsync(pb.eps_v, eps_vir, v * sizeof(double), kd, ex.stream));
-    if (ex.prec == TCORR_FP64) {
+    if (fp64_epilogue(ex.prec)) {
         dalloc(ex, pb.t1, (size_t)o * v * sizeof(double));
         dalloc(ex, pb.ovov, nov2 * sizeof(double));
         CK(cudaMemcpyAsync(pb.t1, t1, (size_t)o * v * sizeof(double), kd, ex.stream));
@@ -198,7 +274,7 @@ void build_schedule(Exec &ex, Problem &pb) {
 // Device bytes of one problem's resident data (operands, epilogue inputs, tables).
 size_t problem_bytes(const Dims &d, int prec) {
     const size_t o = d.o, v = d.v, v2 = v * v;
-    const size_t eb = elem_bytes(prec), parts = prec == TCORR_FP64 ? 1 : 2;
+    const size_t eb = elem_bytes(prec), parts = operand_planes(prec);
     size_t b = parts * eb * (o * v2 * d.dp + o * v2 * d.lp + o * o * v * d.dp + o * o * v * d.lp);
     b += (o * o * v2 + o * v) * u_elem_bytes(prec) + (o + v) * 8 + v * 4;
     const size_t nb = (v + EPI_TE - 1) / EPI_TE;
@@ -244,6 +320,10 @@ void fill_desc(Exec &ex, Problem &pb, int pbt) {
     pb.u_task = (int64_t)3 * pb.dm.v * pb.dm.v * pb.dm.vc;
     if (ex.prec == TCORR_FP64) {
         pb.gemm_units = f64_units_per_task(pb.dm);
+    } else if (ex.prec == TCORR_FP64_OZ) {
+        std::string msg;
+        if (oz_fill_desc(d, pb.op, pb.oz_e, msg) != cudaSuccess) throw Fail{TCORR_EUNSUPPORTED, msg};
+        pb.gemm_units = oz_units_per_task(d);
     } else {
         std::string msg;
         if (tc_fill_desc(d, ex.prec, pb.op, pbt, TC_KB, msg) != cudaSuccess) throw Fail{TCORR_EUNSUPPORTED, msg};
@@ -350,12 +430,13 @@ void launch_plan(Exec &ex, const Plan &pl, const Seg *d_segs, const SumSpan *d_s
         {
             Timer tm(ex, KC_GEMM);
             if (ex.prec == TCORR_FP64) CK(launch_ugemm_f64(w, st));
+            else if (ex.prec == TCORR_FP64_OZ) CK(launch_ugemm_oz(ex.sm_count, w, st));
             else CK(launch_ugemm_tc(ex.prec, ex.sm_count, w, st));
             tm.stop();
         }
         {
             Timer tm(ex, KC_EPI);
-            CK(launch_epilogue(ex.prec, w, st));
+            CK(launch_epilogue(fp64_epilogue(ex.prec) ? TCORR_FP64 : ex.prec, w, st));
             tm.stop();
         }
         {
@@ -397,7 +478,7 @@ tcorr_status check_opts(const tcorr_opts &op, std::string &msg) {
         msg = "test_stall must be 0 or 1";
         return TCORR_EINVAL;
     }
-    if (op.prec < TCORR_FP64 || op.prec > TCORR_BF16X3 || op.batch_tasks < 0 ||
+    if (op.prec < TCORR_FP64 || op.prec > TCORR_FP64_OZ || op.batch_tasks < 0 ||
         (op.host_inputs != 0 && op.host_inputs != 1) || (op.tune != 0 && op.tune != 1) ||
         (op.eager != 0 && op.eager != 1) || op.wave_mb < 0) {
         msg = "invalid option (precision, batch_tasks, host_inputs, tune, eager or wave_mb)";
@@ -424,7 +505,8 @@ void init_exec(Exec &ex, const tcorr_opts &op, void *stream) {
     if (ex.prec != TCORR_FP64 && !tc_supported(ex.cc_major, ex.cc_minor))
         throw Fail{TCORR_EUNSUPPORTED, "mixed precision needs the sm_103 tensor-core path (device is sm_" +
                                            std::to_string(ex.cc_major * 10 + ex.cc_minor) + ")"};
-    if (ex.prec != TCORR_FP64) CK(tc_prepare(ex.prec));  // kernel attributes, before any capture
+    if (is_split(ex.prec)) CK(tc_prepare(ex.prec));  // kernel attributes, before any capture
+    if (ex.prec == TCORR_FP64_OZ) CK(oz_prepare());
 }
 
 void build_problem(Exec &ex, Problem &pb, int o, int v, const double *eps_occ, const double *eps_vir,

@@ -43,6 +43,8 @@ struct Problem {
     int norb = 0;              // epilogue block orbits per task
     int *orbits = nullptr;     // device [norb][3]
     int64_t u_task = 0;        // U elements per task: 3 v v vc
+    unsigned long long *oz_max = nullptr;  // FP64 emulation: device [3] max |vvvo|, |t2|, |ooov| (bit patterns)
+    int *oz_e = nullptr;                   // FP64 emulation: device [2] scale exponents
     int64_t gemm_units = 0;    // W-contraction work units per task
     InstDesc desc{};           // host copy
 };
@@ -150,6 +152,8 @@ const double *device_view(Exec &ex, const double *src, size_t n, bool host, doub
 void free_tmp(Exec &ex, double *&tmp, size_t n);
 void resolve_timers(Exec &ex);
 int elem_kind(int prec);
+bool is_split(int prec);     // TF32x3 / BF16x3 (hi + lo operands, FP32 U and epilogue)
+bool fp64_epilogue(int prec);  // FP64 and FP64 emulation: FP64 U, epilogue inputs and epilogue
 size_t elem_bytes(int prec);
 size_t u_elem_bytes(int prec);
 Dims make_dims(int o, int v);

@@ -1,0 +1,263 @@
+// Device helpers shared by the tcgen05 kernels (W contractions in split
+// precision and in FP64 emulation): bounded mbarrier waits, TMA loads, tcgen05
+// MMA / commit / TMEM loads, shared-memory matrix descriptors, the work-item
+// decode of a wave, and host-side tensor-map encoding.
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <string>
+
+#include "tcorr_internal.cuh"
+
+namespace tcorr {
+namespace tcx {
+
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s of wall time per wait ...
+constexpr uint32_t WAIT_MIN_POLLS = 1u << 18;      // ... and at least this many polls, so that time
+                                                   // spent off the GPU (pre-emption) never counts
+
+enum { MAP_G_NAT = 0, MAP_G_SWP, MAP_T2K_NAT, MAP_T2K_SWP, MAP_T2R, MAP_AON, NMAP };
+static_assert(NMAP == 6, "InstDesc::maps holds six operand maps");
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on one mbarrier phase; false on expiry (both the wall-time
+// and the poll limit passed) or when another role has already aborted.
+static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (*abort_flag) return false;
+            if (it >= WAIT_MIN_POLLS && gtimer() - t0 > WAIT_LIMIT_NS) return false;
+        }
+    }
+}
+__device__ __forceinline__ void fail(volatile int *abort_flag, int *err, int code) {
+    *abort_flag = 1;
+    atomicOr(err, code);
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int c0, int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+        "l"(map), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"(map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+// K-major operand tile with 64-byte rows and 64-byte swizzle: 8-row groups
+// are 512 bytes apart (SBO); LBO is unused for swizzled K-major layouts.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+template <int KIND>
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+    if constexpr (KIND == 1) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    }
+}
+// 16 consecutive accumulator columns of this warp's 32 TMEM lanes (the
+// caller waits with tc_wait_ld before reading r)
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+struct SegCache {
+    int si;                    // cached segment (-1: none)
+    int64_t begin, end;        // its item range
+    const InstDesc *d;
+    int64_t task0, u_off;
+    int npass, nct, nbt;
+    int tcached;               // task (index in the segment) whose indices are cached
+    int ti, tj, tk;
+};
+__device__ __forceinline__ void seg_reset(SegCache &c) {
+    c.si = -1;
+    c.tcached = -1;
+}
+__device__ __forceinline__ void seg_update(const Wave &w, int64_t it, SegCache &c) {
+    if (c.si >= 0 && it < c.end) return;
+    int lo = c.si < 0 ? 0 : c.si, hi = w.nseg - 1;  // items only grow: search forward
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (w.segs[mid].gemm0 <= it) lo = mid; else hi = mid - 1;
+    }
+    const Seg &sg = w.segs[lo];
+    c.si = lo;
+    c.begin = sg.gemm0;
+    c.end = lo + 1 < w.nseg ? w.segs[lo + 1].gemm0 : w.n_gemm;
+    c.d = w.descs + sg.inst;
+    c.task0 = sg.task0;
+    c.u_off = sg.u_off;
+    c.npass = c.d->npass;
+    c.nct = c.d->nct;
+    c.nbt = c.d->nbt;
+    c.tcached = -1;
+}
+struct Item {
+    int tb, g, bt, ct, n;
+    int s, p, q;     // (s; p, q) of the group
+    bool diag;       // i = j = k: no work
+};
+__device__ __forceinline__ Item decode(const Wave &w, int64_t it, SegCache &c) {
+    seg_update(w, it, c);
+    Item r;
+    int64_t x = it - c.begin;
+    r.n = (int)(x % c.npass);
+    x /= c.npass;
+    r.ct = (int)(x % c.nct);
+    x /= c.nct;
+    r.bt = (int)(x % c.nbt);
+    x /= c.nbt;
+    r.g = (int)(x % 3);
+    r.tb = (int)(x / 3);
+    if (r.tb != c.tcached) {
+        const int *tk = c.d->tasks + 3 * (c.task0 + r.tb);
+        c.ti = tk[0];
+        c.tj = tk[1];
+        c.tk = tk[2];
+        c.tcached = r.tb;
+    }
+    const int i = c.ti, j = c.tj, k = c.tk;
+    r.diag = (i == j && j == k);
+    if (r.g == 0) { r.s = i; r.p = j; r.q = k; }
+    else if (r.g == 1) { r.s = j; r.p = i; r.q = k; }
+    else { r.s = k; r.p = i; r.q = j; }
+    return r;
+}
+__device__ __forceinline__ int num_chunks(const InstDesc &d) { return 2 * d.kv + 2 * d.ko; }
+// K steps of chunk ch that carry data: the K extent of each segment is padded
+// only to 16, so the last chunk of a segment may hold a single BF16 K step
+// (the rest of its 64-byte rows is TMA zero fill).  kv, ko: chunks of the
+// d and l segments; dp, lp: their padded extents.
+template <int KIND>
+__device__ __forceinline__ int chunk_ksteps(int kv, int ko, int dp, int lp, int ch) {
+    if constexpr (KIND == 1) {
+        return 2;  // TF32: 16 elements per chunk, always all data
+    } else {
+        int kk, kext;
+        if (ch < 2 * kv) { kk = ch < kv ? ch : ch - kv; kext = dp; }
+        else { kk = ch - 2 * kv; kk = kk < ko ? kk : kk - ko; kext = lp; }
+        return kext - kk * 32 >= 32 ? 2 : 1;
+    }
+}
+
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int c0, int c1, int c2, int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(dst),
+        "l"(map), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+}
+// 8 consecutive accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr));
+}
+
+inline PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+inline bool encode(CUtensorMap *m, CUtensorMapDataType dt, int rank, void *base, const uint64_t *dims,
+            const uint64_t *strides_bytes, const uint32_t *box, std::string &err, const char *what) {
+    auto fn = get_encode();
+    if (!fn) {
+        err = "cuTensorMapEncodeTiled unavailable";
+        return false;
+    }
+    uint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = fn(m, dt, (cuuint32_t)rank, base, (const cuuint64_t *)dims, (const cuuint64_t *)strides_bytes,
+                    (const cuuint32_t *)box, (const cuuint32_t *)es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        err = std::string("cuTensorMapEncodeTiled failed for ") + what + " (CUresult " + std::to_string((int)r) + ")";
+        return false;
+    }
+    return true;
+}
+
+
+}  // namespace tcx
+}  // namespace tcorr

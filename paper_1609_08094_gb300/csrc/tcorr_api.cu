@@ -150,7 +150,7 @@ tcorr_status tcorr_create(tcorr_t *out, int o, int v, const double *eps_occ,
         dalloc(ex, ex.partials, (size_t)ex.part_cap * sizeof(double));
         alloc_common(ex);
         fill_desc(ex, pb, model_pb(v));
-        if (ex.prec != TCORR_FP64 && op.tune == 1) fill_desc(ex, pb, tuned_pb(ex, pb));
+        if (is_split(ex.prec) && op.tune == 1) fill_desc(ex, pb, tuned_pb(ex, pb));
         upload_descs(ex, {&pb});
         {   // staging for the largest plan (the whole task list), so that calls do not allocate
             Plan pl = make_plan(ex, {&pb}, {Span{0, 0, pb.ntask}});
@@ -335,9 +335,9 @@ tcorr_status tcorr_batch_create(tcorr_batch_t *out, int n, const tcorr_problem *
             Problem &pb = b->pbs[m];
             build_problem(ex, pb, p.o, p.v, p.eps_occ, p.eps_vir, p.t1, p.t2, p.vvvo, p.ooov, p.ovov,
                           op.host_inputs == 1);
-            const int t = ex.prec == TCORR_FP64 ? 0 : model_pb(p.v);
+            const int t = ex.prec == TCORR_FP64 ? 0 : (is_split(ex.prec) ? model_pb(p.v) : 8);
             fill_desc(ex, pb, t ? t : 8);
-            if (ex.prec != TCORR_FP64 && op.tune == 1) {
+            if (is_split(ex.prec) && op.tune == 1) {
                 const int tt = tuned_pb(ex, pb);
                 fill_desc(ex, pb, tt);
                 b->pbt[m] = tt;
@@ -420,7 +420,7 @@ tcorr_status tcorr_batch_energy(tcorr_batch_t b, double *e_out) {
 tcorr_status tcorr_batch_tile(tcorr_batch_t b, int idx, int *tile) {
     if (!b || !tile || idx < 0 || idx >= (int)b->pbs.size()) return TCORR_EINVAL;
     tile[0] = b->pbt[idx];
-    tile[1] = b->ex.prec == TCORR_FP64 ? 0 : TC_KB;
+    tile[1] = b->ex.prec == TCORR_FP64 ? 0 : (is_split(b->ex.prec) ? TC_KB : 1);
     return TCORR_OK;
 }
 

@@ -69,6 +69,7 @@ struct InstDesc {
     int nbt, nct, npass, kv, ko, brows;
     uint32_t stage_tx;        // TMA bytes per pipeline stage
     int norb;                 // epilogue block orbits per task (cube edge 8)
+    const int *oz_e;          // FP64 emulation: device [2] scale exponents of the A and B operand sides
     const void *G, *T2K, *T2R, *AoN;  // FP64 operand layouts (FP64 W contractions)
     const double *eps_o, *eps_v;
     const void *t1, *ovov;    // FP64 or FP32 copies for the epilogue
@@ -159,6 +160,23 @@ cudaError_t tc_fill_desc(InstDesc &d, int prec, const Operands &op, int pb, int 
 int64_t tc_units_per_task(const InstDesc &d);
 // sets the kernel attributes once per process (call before any stream capture)
 cudaError_t tc_prepare(int prec);
+
+// ---- gemm_oz.cu (FP64 emulation on the BF16 tensor cores) -----------------------
+int oz_slices();  // slice planes per operand
+// *out = max over k of the bit pattern of |x[k]| (out zeroed by the caller)
+cudaError_t launch_maxabs(const double *x, int64_t n, unsigned long long *out, cudaStream_t st);
+// *m = max(*m, bit pattern of |x|) for a value known on the host
+cudaError_t launch_seed_max(unsigned long long *m, double x, cudaStream_t st);
+// e[0], e[1]: scale exponents of the A side (m[0] vvvo, m[1] t2) and B side (m[1] t2, m[2] ooov)
+cudaError_t launch_oz_exponents(const unsigned long long *m, int *e, cudaStream_t st);
+// out[p*plane + b*ob + c*oc + r] = slice p of sign * 2^-e[0] * in[b*sb + r*sr + c*sc], r < Rp (zero for r >= R)
+cudaError_t launch_slice_pad(const double *in, void *out, int64_t B, int R, int Rp, int64_t C, int64_t sb,
+                             int64_t sr, int64_t sc, int64_t ob, int64_t oc, int64_t plane, const int *e,
+                             double sign, cudaStream_t st);
+cudaError_t oz_fill_desc(InstDesc &d, const Operands &op, const int *exps, std::string &err);
+int64_t oz_units_per_task(const InstDesc &d);
+cudaError_t oz_prepare();
+cudaError_t launch_ugemm_oz(int sm_count, const Wave &w, cudaStream_t st);
 cudaError_t launch_ugemm_tc(int prec, int sm_count, const Wave &w, cudaStream_t st);
 
 }  // namespace tcorr

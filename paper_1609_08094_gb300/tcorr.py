@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _build
 
-PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
+PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2, "fp64_oz": 3}
 STATUS = ["TCORR_OK", "TCORR_EINVAL", "TCORR_ENOMEM", "TCORR_ECUDA", "TCORR_ETIMEOUT",
           "TCORR_EUNSUPPORTED"]
 KERNEL_CLASSES = ("prep", "gemm", "epilogue", "reduce")
