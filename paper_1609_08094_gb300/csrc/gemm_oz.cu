@@ -28,7 +28,7 @@
 // rows, 64-byte K rows) and S B planes (OZ_N rows of a) with 5-D / 4-D tensor
 // maps whose outermost coordinate is the slice; warp 1 issues the S(S+1)/2
 // slice-pair MMAs (M = 128, N = OZ_N) into the S weight accumulators of a
-// double-buffered TMEM block; warps 2-9 drain and accumulate.  Every wait is
+// TMEM block of OZ_KB chunks; warps 2-9 drain and accumulate.  Every wait is
 // bounded as in the split-precision kernel.
 #include <cuda_bf16.h>
 
@@ -45,7 +45,7 @@ using namespace tcx;
 
 constexpr int OZ_S = 5;          // slices per operand
 constexpr int OZ_BETA = 7;       // bits per slice
-constexpr int OZ_N = 48;         // a columns per item
+constexpr int OZ_N = 96;         // a columns per item
 constexpr int OZ_THREADS = 320;
 constexpr int OZ_EPI = 256;      // warps 2-9
 constexpr int OZ_BM = 128;       // pair rows per tile
@@ -55,9 +55,10 @@ constexpr int OZ_B = OZ_N * OZ_ROW;         // 3 KB per B plane
 constexpr int OZ_STAGE = OZ_S * (OZ_A + OZ_B);
 constexpr int OZ_STAGES = 3;
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024;
-constexpr int OZ_BUF = 256;      // TMEM columns per accumulator buffer
 constexpr int OZ_HALF = OZ_N / 2;  // columns per epilogue warp
-static_assert(OZ_S * OZ_N <= OZ_BUF, "weight accumulators of one buffer exceed 256 TMEM columns");
+// One TMEM accumulator block of OZ_S weights x OZ_N columns (single-buffered:
+// a block spans OZ_KB chunks, so its drain is short against its MMAs)
+static_assert(OZ_S * OZ_N <= 512, "weight accumulators exceed the 512 TMEM columns");
 static_assert(OZ_A % 1024 == 0 && OZ_B % 1024 == 0, "planes keep the 64-byte swizzle pattern aligned");
 constexpr int OZ_KB = 8;         // K chunks accumulated in TMEM per block (exact, see below)
 // Exactness of a block's weight sums in FP32: |a_1| <= 2^beta, |a_i| <= 2^(beta-1)
@@ -65,7 +66,7 @@ constexpr int OZ_KB = 8;         // K chunks accumulated in TMEM per block (exac
 // at most S pairs each with one factor <= 2^(beta-1).
 static_assert(32 * OZ_KB * (1 << (2 * OZ_BETA)) < (1 << 24), "weight (1,1) must stay exact in FP32");
 static_assert(OZ_S * 32 * OZ_KB * (1 << (2 * OZ_BETA - 1)) < (1 << 24), "weight sums must stay exact in FP32");
-static_assert(OZ_HALF == 24, "the drain below loads 16 + 8 columns");
+static_assert(OZ_HALF % 16 == 0, "the drain loads 16 columns at a time");
 
 
 __global__ void __launch_bounds__(OZ_THREADS, 1) ugemm_oz_kernel(const __grid_constant__ Wave wv) {
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ugemm_oz_kernel(const __grid_co
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t hblk = 0;  // blocks of OZ_KB chunks issued: buffer hblk & 1, phase (hblk >> 1) & 1
+            uint32_t hblk = 0;  // blocks of OZ_KB chunks issued: accumulator phase hblk & 1
             bool ok = true;
             SegCache sc;
             seg_reset(sc);
@@ -185,7 +186,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ugemm_oz_kernel(const __grid_co
                 const int nch = 2 * kv + 2 * ko;
                 for (int c0 = 0; c0 < nch && ok; c0 += OZ_KB) {
                     const int nb = min(OZ_KB, nch - c0);
-                    const uint32_t buf = hblk & 1u;
                     for (int cb = 0; cb < nb; cb++) {
                         const int ch = c0 + cb;
                         if (!mbar_wait(smem_u32(&bar_full[stage]), phase, &abort_sh)) {
@@ -193,8 +193,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ugemm_oz_kernel(const __grid_co
                             ok = false;
                             break;
                         }
-                        if (cb == 0 &&
-                            !mbar_wait(smem_u32(&bar_hempty[buf]), ((hblk >> 1) & 1u) ^ 1u, &abort_sh)) {
+                        if (cb == 0 && !mbar_wait(smem_u32(&bar_hempty[0]), (hblk & 1u) ^ 1u, &abort_sh)) {
                             fail(&abort_sh, wv.err, DERR_TIMEOUT_TMEM);
                             ok = false;
                             break;
@@ -205,7 +204,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ugemm_oz_kernel(const __grid_co
                         // descriptors are linear in the address (its low field is addr >> 4), so every
                         // plane / K-step descriptor is the stage's base descriptor plus a constant
                         const uint64_t dA = sdesc(sA), dB = sdesc(sB);
-                        const uint32_t dt0 = tmem + buf * (uint32_t)OZ_BUF;
+                        const uint32_t dt0 = tmem;
 #pragma unroll
                         for (int t = 0; t < OZ_S; t++) {
                             // the slice pairs of weight t: (i - 1) + (j - 1) = t, both in 0 .. S-1
@@ -227,7 +226,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ugemm_oz_kernel(const __grid_co
                         if (++stage == OZ_STAGES) { stage = 0; phase ^= 1u; }
                     }
                     if (!ok) break;
-                    tc_commit(smem_u32(&bar_hfull[buf]));
+                    tc_commit(smem_u32(&bar_hfull[0]));
                     hblk++;
                 }
             }
@@ -258,30 +257,27 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ugemm_oz_kernel(const __grid_co
 #pragma unroll
             for (int j = 0; j < OZ_HALF; j++) tot[j] = 0;
             for (int hb = 0; hb < nhb; hb++) {
-                const uint32_t buf = hblk & 1u;
                 int good = 1;
-                if (lane == 0) good = mbar_wait(smem_u32(&bar_hfull[buf]), (hblk >> 1) & 1u, &abort_sh) ? 1 : 0;
+                if (lane == 0) good = mbar_wait(smem_u32(&bar_hfull[0]), hblk & 1u, &abort_sh) ? 1 : 0;
                 good = __shfl_sync(0xffffffffu, good, 0);
                 __syncwarp();
                 if (!good) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll
                 for (int t = 0; t < OZ_S; t++) {
-                    uint32_t r[16], r2[8];
-                    const uint32_t ta = tmem + lane_off + buf * (uint32_t)OZ_BUF + (uint32_t)(t * OZ_N + half * OZ_HALF);
-                    tc_ld16(ta, r);
-                    tc_ld8(ta + 16, r2);
-                    tc_wait_ld();
                     const long long wgt = 1LL << (OZ_BETA * (OZ_S - 1 - t));
 #pragma unroll
-                    for (int j = 0; j < 16; j++)
-                        tot[j] += (long long)__float2int_rn(__uint_as_float(r[j])) * wgt;
+                    for (int c16 = 0; c16 < OZ_HALF / 16; c16++) {
+                        uint32_t r[16];
+                        tc_ld16(tmem + lane_off + (uint32_t)(t * OZ_N + half * OZ_HALF + c16 * 16), r);
+                        tc_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 8; j++)
-                        tot[16 + j] += (long long)__float2int_rn(__uint_as_float(r2[j])) * wgt;
+                        for (int j = 0; j < 16; j++)
+                            tot[c16 * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) * wgt;
+                    }
                 }
                 tc_fence_before();
-                mbar_arrive(smem_u32(&bar_hempty[buf]));
+                mbar_arrive(smem_u32(&bar_hempty[0]));
                 hblk++;
             }
             if (!ok) {
