@@ -54,7 +54,6 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const Wave wv) {
     constexpr int CUBE = TE * TE * TP;       // smem elements per cube
     constexpr int NE = TE * TE * TE;         // elements per cube
     __shared__ int comp[6][6];
-    __shared__ int blk[6][3];
     __shared__ int distinct[6];
     __shared__ double red[NT / 32][2];
 
@@ -72,51 +71,70 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const Wave wv) {
         return;
     }
     const int tid = threadIdx.x;
-    const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-    if (tid < 36) {
-        const int pi = tid / 6, q = tid % 6;
-        const int t0 = P[pi][P[q][0]], t1 = P[pi][P[q][1]], t2 = P[pi][P[q][2]];
-        int sig = 0;
-        for (int s = 0; s < 6; s++)
-            if (P[s][0] == t0 && P[s][1] == t1 && P[s][2] == t2) sig = s;
-        comp[pi][q] = sig;
-    }
-    if (tid < 6) {
-        const int ob[3] = {p.orbits[3 * orb], p.orbits[3 * orb + 1], p.orbits[3 * orb + 2]};
-        blk[tid][0] = ob[P[tid][0]];
-        blk[tid][1] = ob[P[tid][1]];
-        blk[tid][2] = ob[P[tid][2]];
-    }
-    __syncthreads();
-    if (tid < 6) {
-        int d = 1;
-        for (int s = 0; s < tid; s++)
-            if (blk[s][0] == blk[tid][0] && blk[s][1] == blk[tid][1] && blk[s][2] == blk[tid][2]) d = 0;
-        distinct[tid] = d;
-    }
-
+    // the orbit's blocks in registers (every thread reads them), so the U loads
+    // below are issued before any barrier
+    const int ob0 = p.orbits[3 * orb], ob1 = p.orbits[3 * orb + 1], ob2 = p.orbits[3 * orb + 2];
+#define OBP(s, d) pick3(ob0, ob1, ob2, perm_pos((s), (d)))
     const UT *U0 = static_cast<const UT *>(wv.U) + sg.u_off + (int64_t)(tb * 3 + 0) * v2 * vc;
     const UT *U1 = U0 + v2 * vc;
     const UT *U2 = U1 + v2 * vc;
-
-    // pass A: W = U0[x][y][z] + U1[y][x][z]   (z fastest: contiguous rows)
-    for (int e = tid; e < 6 * NE; e += NT) {
-        const int s = e / NE, l = e % NE;
+    static_assert(sizeof(UT) == 8 && TE == 8, "16-byte loads of 8-element FP64 rows");
+    // pass A loads: W = U0[x][y][z] + U1[y][x][z] (z fastest, pairs of z); pass B
+    // loads: U2[z][x][y] (y fastest, pairs of y).  A row never ends within a
+    // pair (rows are padded to 16), so a pair that starts inside [0, v) is in bounds.
+    double2 ra[6], rb[6], rc[6];
+#pragma unroll
+    for (int it = 0; it < 6; it++) {
+        const int e2 = tid + it * NT;             // 6 slots x 256 pairs
+        const int s = e2 >> 8, l = (e2 & 255) * 2;
         const int l0 = l / (TE * TE), l1 = (l / TE) % TE, l2 = l % TE;
-        const int x = blk[s][0] * TE + l0, y = blk[s][1] * TE + l1, z = blk[s][2] * TE + l2;
-        CT w = CT(0);
-        if (x < v && y < v && z < v)
-            w = CT(U0[((int64_t)x * v + y) * vc + z]) + CT(U1[((int64_t)y * v + x) * vc + z]);
-        Ws[s * CUBE + (l0 * TE + l1) * TP + l2] = w;
+        const int x = OBP(s, 0) * TE + l0, y = OBP(s, 1) * TE + l1, z = OBP(s, 2) * TE + l2;
+        ra[it] = rb[it] = rc[it] = make_double2(0.0, 0.0);
+        if (x < v && y < v && z < v) {
+            ra[it] = __ldg(reinterpret_cast<const double2 *>(U0 + ((int64_t)x * v + y) * vc + z));
+            rb[it] = __ldg(reinterpret_cast<const double2 *>(U1 + ((int64_t)y * v + x) * vc + z));
+        }
+        // pass B element pair: (l2', l0', l1') with y fastest
+        const int m2 = l / (TE * TE), m0 = (l / TE) % TE, m1 = l % TE;
+        const int xb = OBP(s, 0) * TE + m0, yb = OBP(s, 1) * TE + m1, zb = OBP(s, 2) * TE + m2;
+        if (xb < v && yb < v && zb < v)
+            rc[it] = __ldg(reinterpret_cast<const double2 *>(U2 + ((int64_t)zb * v + xb) * vc + yb));
+    }
+    if (tid < 36) {  // comp[pi][q]: the slot of permutation pi composed with q
+        const int pi = tid / 6, q = tid % 6;
+        const int t0 = perm_pos(pi, perm_pos(q, 0)), t1v = perm_pos(pi, perm_pos(q, 1));
+        int sig = 0;
+        for (int s2 = 0; s2 < 6; s2++)
+            if (perm_pos(s2, 0) == t0 && perm_pos(s2, 1) == t1v) sig = s2;
+        comp[pi][q] = sig;
+    }
+    if (tid >= 64 && tid < 70) {
+        const int t = tid - 64;
+        int d = 1;
+        for (int s2 = 0; s2 < t; s2++)
+            if (OBP(s2, 0) == OBP(t, 0) && OBP(s2, 1) == OBP(t, 1) && OBP(s2, 2) == OBP(t, 2)) d = 0;
+        distinct[t] = d;
+    }
+#pragma unroll
+    for (int it = 0; it < 6; it++) {
+        const int e2 = tid + it * NT;
+        const int s = e2 >> 8, l = (e2 & 255) * 2;
+        const int l0 = l / (TE * TE), l1 = (l / TE) % TE, l2 = l % TE;
+        const int z = OBP(s, 2) * TE + l2;
+        CT *wp = Ws + s * CUBE + (l0 * TE + l1) * TP + l2;
+        wp[0] = (z < v) ? CT(ra[it].x) + CT(rb[it].x) : CT(0);     // row padding is not data
+        wp[1] = (z + 1 < v) ? CT(ra[it].y) + CT(rb[it].y) : CT(0);
     }
     __syncthreads();
-    // pass B: W += U2[z][x][y]   (y fastest: contiguous rows)
-    for (int e = tid; e < 6 * NE; e += NT) {
-        const int s = e / NE, l = e % NE;
-        const int l2 = l / (TE * TE), l0 = (l / TE) % TE, l1 = l % TE;
-        const int x = blk[s][0] * TE + l0, y = blk[s][1] * TE + l1, z = blk[s][2] * TE + l2;
-        if (x < v && y < v && z < v)
-            Ws[s * CUBE + (l0 * TE + l1) * TP + l2] += CT(U2[((int64_t)z * v + x) * vc + y]);
+#pragma unroll
+    for (int it = 0; it < 6; it++) {
+        const int e2 = tid + it * NT;
+        const int s = e2 >> 8, l = (e2 & 255) * 2;
+        const int m2 = l / (TE * TE), m0 = (l / TE) % TE, m1 = l % TE;
+        const int yb = OBP(s, 1) * TE + m1;
+        CT *wp = Ws + s * CUBE + (m0 * TE + m1) * TP + m2;
+        if (yb < v) wp[0] += CT(rc[it].x);
+        if (yb + 1 < v) wp[TP] += CT(rc[it].y);
     }
     __syncthreads();
 
@@ -131,11 +149,11 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const Wave wv) {
     const int64_t ovs = (int64_t)o * v;
 
     double s4 = 0.0, c4 = 0.0, s5 = 0.0, c5 = 0.0;
-    if (blk[0][0] < blk[0][1] && blk[0][1] < blk[0][2]) {
+    if (ob0 < ob1 && ob1 < ob2) {
         // distinct blocks A < B < C: element orbits; slot q holds the element
         // with indices ordered as q (abc, acb, bac, bca, cab, cba); even slots
         // 0, 3, 4, odd 1, 2, 5; Z_q = 6 w_q + 2E - 4O (even) or 6 w_q + 2O - 4E (odd)
-        const int A0 = blk[0][0] * TE, B0 = blk[0][1] * TE, C0 = blk[0][2] * TE;
+        const int A0 = ob0 * TE, B0 = ob1 * TE, C0 = ob2 * TE;
         CT a4 = CT(0), a5 = CT(0);
         for (int l = tid; l < NE; l += NT) {
             const int la = l / (TE * TE), lb = (l / TE) % TE, lc = l % TE;
@@ -179,7 +197,7 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const Wave wv) {
     for (int s = 0; s < 6; s++) {
         if (!distinct[s]) continue;
         CT a4 = CT(0), a5 = CT(0);
-        const int X0 = blk[s][0] * TE, Y0 = blk[s][1] * TE, Z0 = blk[s][2] * TE;
+        const int X0 = OBP(s, 0) * TE, Y0 = OBP(s, 1) * TE, Z0 = OBP(s, 2) * TE;
         for (int l = tid; l < NE; l += NT) {
             const int lv0 = l / (TE * TE), lv1 = (l / TE) % TE, lv2 = l % TE;
             const int x = X0 + lv0, y = Y0 + lv1, z = Z0 + lv2;
@@ -218,6 +236,8 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const Wave wv) {
     }
 }
 
+
+#undef OBP
 
 // Mixed-precision epilogue: the same block-orbit algorithm with 8^3 cubes in
 // FP32, sized for occupancy (about 20 KB of shared memory, 48 registers: 5
