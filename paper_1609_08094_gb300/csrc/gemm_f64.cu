@@ -131,23 +131,43 @@ __global__ void __launch_bounds__(NT) ugemm_f64_kernel(const Wave w) {
 #pragma unroll
         for (int c = 0; c < 4; c++) acc[r][c] = 0.0;
 
+    // Padding costs FP64-pipe time only where a warp issues it: a warp whose
+    // four a values all lie at or past v (the ragged last a tile) issues no
+    // FMA, and the last chunk of each K segment stops at the segment's end
+    // (the zero padding of d to a multiple of KC and of l is never multiplied).
+    const bool active = a0 + ta * 4 < v;
+    auto mma_step = [&](int k) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) av[r] = As[k][tp + 32 * r];
+        const double2 b01 = *reinterpret_cast<const double2 *>(&Bs[k][ta * 4]);
+        const double2 b23 = *reinterpret_cast<const double2 *>(&Bs[k][ta * 4 + 2]);
+        bv[0] = b01.x; bv[1] = b01.y; bv[2] = b23.x; bv[3] = b23.y;
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+    };
+    const int tail_v = v - (nchunk_v - 1) * KC, tail_o = o - (nchunk_o - 1) * KC;
+
     load_chunk(0);
     for (int chunk = 0; chunk < nchunk; chunk++) {
         store_chunk();
         __syncthreads();
         if (chunk + 1 < nchunk) load_chunk(chunk + 1);
+        // valid k of this chunk: KC except at the end of a segment
+        int kn = KC;
+        if (chunk == nchunk_v - 1 || chunk == 2 * nchunk_v - 1) kn = tail_v;
+        else if (chunk == 2 * nchunk_v + nchunk_o - 1 || chunk == nchunk - 1) kn = tail_o;
+        if (active) {
+            if (kn == KC) {
 #pragma unroll
-        for (int k = 0; k < KC; k++) {
-            double av[4], bv[4];
+                for (int k = 0; k < KC; k++) mma_step(k);
+            } else {
 #pragma unroll
-            for (int r = 0; r < 4; r++) av[r] = As[k][tp + 32 * r];
-            const double2 b01 = *reinterpret_cast<const double2 *>(&Bs[k][ta * 4]);
-            const double2 b23 = *reinterpret_cast<const double2 *>(&Bs[k][ta * 4 + 2]);
-            bv[0] = b01.x; bv[1] = b01.y; bv[2] = b23.x; bv[3] = b23.y;
-#pragma unroll
-            for (int r = 0; r < 4; r++)
-#pragma unroll
-                for (int c = 0; c < 4; c++) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+                for (int k = 0; k < KC; k++)
+                    if (k < kn) mma_step(k);
+            }
         }
         __syncthreads();
     }

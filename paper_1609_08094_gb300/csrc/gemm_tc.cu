@@ -32,7 +32,9 @@
 //   warps 2-9: two warps per TMEM lane quarter, 128 columns each: drain each
 //             block into the register total, then store the U rows (rows of
 //             16 consecutive c, coalesced) at the end of the tile.
-// A work item is (task, group, pair tile, N pass of 256 a values).  Every
+// A work item is (task, group, pair tile, N pass).  The v values of a are cut
+// into ceil(v / 256) passes of equal width (a multiple of 16, at most 256), so
+// the B tiles carry no more padding rows than the rounding needs.  Every
 // mbarrier wait is bounded (wall clock): on expiry the kernel sets an error
 // flag, stops all roles, waits (bounded) for its own copies in flight, frees
 // TMEM and returns; the host reports TCORR_ETIMEOUT.
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                 const InstDesc &d = *sc.d;
                 const int o = d.dm.o, kv = d.kv, ko = d.ko, nch = num_chunks(d);
                 const int s = w.s, pp = w.p, q = w.q;
-                const int cb = w.bt * d.pb, cc = w.ct * d.pc, ca = w.n * BN;
+                const int cb = w.bt * d.pb, cc = w.ct * d.pc, ca = w.n * d.brows;
                 const uint32_t stage_tx = d.stage_tx;
                 for (int ch = 0; ch < nch; ch++) {
                     if (!mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1u, &abort_sh)) {
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                 // per-item constants in registers: the issue loop reads no memory
                 const int kv = d.kv, ko = d.ko, dp = d.dm.dp, lp = d.dm.lp;
                 const int nch = 2 * kv + 2 * ko, kb = d.kb;
-                const int nvalid = min(BN, d.dm.v - w.n * BN);
+                const int nvalid = min(d.brows, d.dm.v - w.n * d.brows);
                 const int N = (nvalid + 15) / 16 * 16;
                 const uint32_t idesc = idesc_base | ((uint32_t)(N >> 3) << 17);
                 // K blocks of kb chunks: the small hi*lo and lo*hi products of each
@@ -268,7 +270,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
             const int lb = row / d.pc, lc = row % d.pc;
             // the two warps of a lane quarter split the accumulator's N columns:
             // 128 each for N > 128, else 32 or 64 each (only columns < N are read)
-            const int N = (min(BN, v - w.n * BN) + 15) / 16 * 16;
+            const int pass0 = w.n * d.brows, pass_end = min(v, pass0 + d.brows);
+            const int N = (pass_end - pass0 + 15) / 16 * 16;
             const int wh = N > 128 ? 128 : (N > 64 ? 64 : 32);
             const int nld = wh / 32;
             float total[128];
@@ -309,12 +312,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
             // [a][b][c] order, group 1 at [b][a][c] (aligned with W, see tcorr_internal.cuh)
             const int b = w.bt * d.pb + lb, c = w.ct * d.pc + lc;
             if (b < v && c < v) {
-                const int a0 = w.n * BN + half * wh;
+                const int a0 = pass0 + half * wh;
                 const int64_t stride = w.g == 1 ? (int64_t)vc : (int64_t)v * vc;
                 const int64_t base = w.g == 1 ? (int64_t)b * v * vc + c : (int64_t)b * vc + c;
                 const int64_t u_off = u_seg + (int64_t)(w.tb * 3 + w.g) * v * v * vc;
                 float *Ug = static_cast<float *>(wv.U) + u_off + base + (int64_t)a0 * stride;
-                const int na = min(wh, v - a0);
+                const int na = min(wh, pass_end - a0);
                 if (na == 128) {
 #pragma unroll
                     for (int j = 0; j < 128; j++) {
@@ -368,9 +371,9 @@ cudaError_t tc_fill_desc(InstDesc &d, int prec, const Operands &op, int pb, int 
     d.nbt = (v + pb - 1) / pb;
     d.nct = (v + pc - 1) / pc;
     d.npass = (v + BN - 1) / BN;
+    d.brows = round_up((v + d.npass - 1) / d.npass, 16);  // pass width: <= BN
     d.kv = (v + kch - 1) / kch;
     d.ko = (o + kch - 1) / kch;
-    d.brows = std::min(BN, round_up(v, 16));
     d.stage_tx = (uint32_t)(2 * A_BYTES + 2 * d.brows * ROW_BYTES);
     const uint64_t V = v, O = o;
     const uint32_t bk = (uint32_t)kch, bpc = (uint32_t)pc, bpb = (uint32_t)pb, brows = (uint32_t)d.brows;

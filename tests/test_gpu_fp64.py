@@ -32,6 +32,7 @@ def run(inst, **kw):
     (4, 20, 72, 1),        # small configuration (o=4, v=20, naux=72)
     (3, 7, None, 2), (5, 13, None, 3), (2, 33, None, 4), (6, 17, None, 5),
     (7, 9, None, 6), (3, 40, None, 7), (1, 5, None, 8), (4, 1, None, 9), (2, 2, None, 10),
+    (3, 130, None, 14),    # a tiles of 32: the last holds 2 of its 32 values (as at v = 450)
 ])
 def test_fp64_matches_oracle(o, v, naux, seed):
     inst = synth.make_instance(o, v, naux, seed)
