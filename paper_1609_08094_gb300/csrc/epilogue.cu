@@ -262,7 +262,7 @@ constexpr int FSLOT = F8 * FP0;     // floats per cube slot
 __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wave wv) {
     __shared__ float Ws[6 * FSLOT];
     __shared__ float T1s[3][3][F8];          // [occupied i,j,k][orbit block][local]
-    __shared__ float OVs[3][3][3][F8 * F8];  // [(jk),(ik),(ij)][block][block][8x8]
+    __shared__ __align__(16) float OVs[3][3][3][F8 * F8];  // [(jk),(ik),(ij)][block][block][8x8]
     __shared__ float Dls[3][F8];             // [orbit block][local] block-relative energies
     __shared__ float base_s;
     __shared__ int comp[6][6];
@@ -331,28 +331,29 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
         const double eijk = p.eps_o[ti] + p.eps_o[tj] + p.eps_o[tkk];
         base_s = (float)(eijk - p.eps_v[ob0 * F8] - p.eps_v[ob1 * F8] - p.eps_v[ob2 * F8]);
     }
-    // stage t1, ovov sub-blocks and block-relative energies
+    // stage t1, ovov sub-blocks and block-relative energies.  The FP32 inputs
+    // are zero padded to vp (t1 rows [p][x], ovov slabs [p][q][x][z]): every
+    // orbit block lies inside, and a sub-block row is two aligned float4 loads.
+    const int vp = (v + F8 - 1) / F8 * F8;
     const float *t1 = static_cast<const float *>(p.t1);
     const float *ov = static_cast<const float *>(p.ovov);
-    for (int e = tid; e < 3 * 3 * F8; e += NT) {
-        const int oc = e / (3 * F8), b = (e / F8) % 3, m = e % F8;
-        const int x = pick3(ob0, ob1, ob2, b) * F8 + m;
+    if (tid < 3 * 3 * F8) {
+        const int oc = tid / (3 * F8), b = (tid / F8) % 3, m = tid % F8;
         const int occ = oc == 0 ? ti : (oc == 1 ? tj : tkk);
-        T1s[oc][b][m] = x < v ? t1[occ * v + x] : 0.f;
-    }
-    for (int e = tid; e < 3 * F8; e += NT) {
-        const int b = e / F8, m = e % F8, x = pick3(ob0, ob1, ob2, b) * F8 + m;
+        T1s[oc][b][m] = t1[occ * vp + pick3(ob0, ob1, ob2, b) * F8 + m];
+    } else if (tid >= 96 + 32 && tid < 96 + 32 + 3 * F8) {
+        const int e = tid - 128, b = e / F8, m = e % F8, x = pick3(ob0, ob1, ob2, b) * F8 + m;
         Dls[b][m] = x < v ? p.dev_f[x] : 0.f;
     }
-    // slices: 0 = (j y | k z), 1 = (i x | k z), 2 = (i x | j y)
-    for (int e = tid; e < 3 * 9 * F8 * F8; e += NT) {
-        const int sl = e / (9 * 64), bb = (e / 64) % 9, m = (e / 8) % 8, n = e % 8;
-        const int ba = bb / 3, bc = bb % 3;
-        const int r = pick3(ob0, ob1, ob2, ba) * F8 + m, c = pick3(ob0, ob1, ob2, bc) * F8 + n;
+    // slices: 0 = (j y | k z), 1 = (i x | k z), 2 = (i x | j y); 3 x 9 sub-blocks
+    // x 8 rows x 2 halves = 432 float4
+    for (int e = tid; e < 3 * 9 * F8 * 2; e += NT) {
+        const int sl = e / 144, rem = e - sl * 144, bb = rem >> 4, m = (rem >> 1) & 7, h = rem & 1;
+        const int ba = bb / 3, bc = bb - 3 * ba;
+        const int r = pick3(ob0, ob1, ob2, ba) * F8 + m, c = pick3(ob0, ob1, ob2, bc) * F8 + 4 * h;
         const int first = sl == 0 ? tj : ti, second = sl == 2 ? tj : tkk;
-        float val = 0.f;
-        if (r < v && c < v) val = ov[(((int64_t)first * v + r) * o + second) * v + c];
-        OVs[sl][ba][bc][m * F8 + n] = val;
+        const float4 val = __ldg(reinterpret_cast<const float4 *>(ov + ((int64_t)(first * o + second) * vp + r) * vp + c));
+        *reinterpret_cast<float4 *>(&OVs[sl][ba][bc][m * F8 + 4 * h]) = val;
     }
 
 #pragma unroll
@@ -388,29 +389,38 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
         // even slots 0,3,4, odd slots 1,2,5.  With E and O the sums of W over
         // the even and odd slots, Z at slot q is 6 w_q + 2E - 4O (q even) or
         // 6 w_q + 2O - 4E (q odd), and all six share one denominator.
+        // thread: fixed (b, c) = (lb, lc), a = la0 and la0 + 4 (the 512 element
+        // orbits of the cube over 256 threads); what depends only on b and c is
+        // read once
         const int A0 = ob0 * F8, B0 = ob1 * F8, C0 = ob2 * F8;
-        for (int l = tid; l < 512; l += NT) {
-            const int la = l >> 6, lb = (l >> 3) & 7, lc = l & 7;
-            if (A0 + la >= v || B0 + lb >= v || C0 + lc >= v) continue;
+        const int lb = (tid >> 3) & 7, lc = tid & 7, la0 = tid >> 6;
+#define OVV(sl, pu, pw, lu, lw) OVs[sl][pu][pw][(lu) * F8 + (lw)]
+        const float tib = T1s[0][1][lb], tic = T1s[0][2][lc];
+        const float tjb = T1s[1][1][lb], tjc = T1s[1][2][lc];
+        const float tkb = T1s[2][1][lb], tkc = T1s[2][2][lc];
+        const float jk_bc = OVV(0, 1, 2, lb, lc), jk_cb = OVV(0, 2, 1, lc, lb);
+        const float ik_bc = OVV(1, 1, 2, lb, lc), ik_cb = OVV(1, 2, 1, lc, lb);
+        const float ij_bc = OVV(2, 1, 2, lb, lc), ij_cb = OVV(2, 2, 1, lc, lb);
+        const float dbc = base + (Dls[1][lb] + Dls[2][lc]);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int la = la0 + 4 * h;
+            if (A0 + la >= v || B0 + lb >= v || C0 + lc >= v) break;  // a grows with h
             const float w0 = Ws[0 * FSLOT + la * FP0 + lb * FP1 + lc];
             const float w1 = Ws[1 * FSLOT + la * FP0 + lc * FP1 + lb];
             const float w2 = Ws[2 * FSLOT + lb * FP0 + la * FP1 + lc];
             const float w3 = Ws[3 * FSLOT + lb * FP0 + lc * FP1 + la];
             const float w4 = Ws[4 * FSLOT + lc * FP0 + la * FP1 + lb];
             const float w5 = Ws[5 * FSLOT + lc * FP0 + lb * FP1 + la];
-            // t1 of occupied i, j, k at a, b, c
-            const float tia = T1s[0][0][la], tib = T1s[0][1][lb], tic = T1s[0][2][lc];
-            const float tja = T1s[1][0][la], tjb = T1s[1][1][lb], tjc = T1s[1][2][lc];
-            const float tka = T1s[2][0][la], tkb = T1s[2][1][lb], tkc = T1s[2][2][lc];
-            // (j u | k w), (i u | k w), (i u | j w) for ordered pairs of {a, b, c}
-#define OVV(sl, pu, pw, lu, lw) OVs[sl][pu][pw][(lu) * F8 + (lw)]
-            const float jk_bc = OVV(0, 1, 2, lb, lc), jk_cb = OVV(0, 2, 1, lc, lb), jk_ac = OVV(0, 0, 2, la, lc);
-            const float jk_ca = OVV(0, 2, 0, lc, la), jk_ab = OVV(0, 0, 1, la, lb), jk_ba = OVV(0, 1, 0, lb, la);
-            const float ik_bc = OVV(1, 1, 2, lb, lc), ik_cb = OVV(1, 2, 1, lc, lb), ik_ac = OVV(1, 0, 2, la, lc);
-            const float ik_ca = OVV(1, 2, 0, lc, la), ik_ab = OVV(1, 0, 1, la, lb), ik_ba = OVV(1, 1, 0, lb, la);
-            const float ij_bc = OVV(2, 1, 2, lb, lc), ij_cb = OVV(2, 2, 1, lc, lb), ij_ac = OVV(2, 0, 2, la, lc);
-            const float ij_ca = OVV(2, 2, 0, lc, la), ij_ab = OVV(2, 0, 1, la, lb), ij_ba = OVV(2, 1, 0, lb, la);
-#undef OVV
+            // t1 of occupied i, j, k at a (at b and c above)
+            const float tia = T1s[0][0][la], tja = T1s[1][0][la], tka = T1s[2][0][la];
+            // (j u | k w), (i u | k w), (i u | j w) for the ordered pairs of {a, b, c} that hold a
+            const float jk_ac = OVV(0, 0, 2, la, lc), jk_ca = OVV(0, 2, 0, lc, la);
+            const float jk_ab = OVV(0, 0, 1, la, lb), jk_ba = OVV(0, 1, 0, lb, la);
+            const float ik_ac = OVV(1, 0, 2, la, lc), ik_ca = OVV(1, 2, 0, lc, la);
+            const float ik_ab = OVV(1, 0, 1, la, lb), ik_ba = OVV(1, 1, 0, lb, la);
+            const float ij_ac = OVV(2, 0, 2, la, lc), ij_ca = OVV(2, 2, 0, lc, la);
+            const float ij_ab = OVV(2, 0, 1, la, lb), ij_ba = OVV(2, 1, 0, lb, la);
             // Y at each ordering q of (a,b,c): t^{q0}_i (j q1|k q2) + t^{q1}_j (i q0|k q2) + t^{q2}_k (i q0|j q1)
             const float y0 = tia * jk_bc + tjb * ik_ac + tkc * ij_ab;
             const float y1 = tia * jk_cb + tjc * ik_ab + tkb * ij_ac;
@@ -423,10 +433,11 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
             const float wy = w0 * y0 + w1 * y1 + w2 * y2 + w3 * y3 + w4 * y4 + w5 * y5;
             const float s4 = 6.f * ww + 2.f * (E * E + O * O) - 8.f * E * O;
             const float s5 = 6.f * wy + (2.f * E - 4.f * O) * (y0 + y3 + y4) + (2.f * O - 4.f * E) * (y1 + y2 + y5);
-            const float r = __fdividef(1.f, base + (Dls[0][la] + Dls[1][lb] + Dls[2][lc]));
+            const float r = __fdividef(1.f, dbc + Dls[0][la]);
             a4 = fmaf(s4, r, a4);
             a5 = fmaf(s5, r, a5);
         }
+#undef OVV
     } else {
         // blocks repeat: element by element over the distinct cube slots
         for (int s = 0; s < 6; s++) {

@@ -69,10 +69,32 @@ __global__ void __launch_bounds__(256) transpose_pad_kernel(
     }
 }
 
-__global__ void to_float_kernel(const double *__restrict__ in, float *__restrict__ out, int64_t n) {
+// FP32 epilogue inputs of the split-precision paths: (p x | q z) as slabs
+// [p][q][x][z] and t1 as rows [p][x], the virtual extents padded with zeros
+// to vp (a multiple of the epilogue's cube edge), so that every 8-wide row of
+// an orbit's sub-block is two aligned 16-byte loads with no bounds test.
+__global__ void ovov_slabs_kernel(const double *__restrict__ in, float *__restrict__ out, int o, int v,
+                                  int vp) {
+    const int64_t n = (int64_t)o * o * vp * vp;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = static_cast<float>(in[i]);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int z = (int)(i % vp);
+        int64_t r = i / vp;
+        const int x = (int)(r % vp);
+        r /= vp;
+        const int q = (int)(r % o), pp = (int)(r / o);
+        out[i] = (x < v && z < v) ? static_cast<float>(in[(((int64_t)pp * v + x) * o + q) * v + z]) : 0.f;
+    }
+}
+
+__global__ void pad_rows_kernel(const double *__restrict__ in, float *__restrict__ out, int rows, int v,
+                                int vp) {
+    const int64_t n = (int64_t)rows * vp;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % vp);
+        out[i] = x < v ? static_cast<float>(in[(i / vp) * v + x]) : 0.f;
+    }
 }
 
 __global__ void block_deltas_kernel(const double *__restrict__ ev, float *__restrict__ d, int v,
@@ -103,10 +125,11 @@ cudaError_t launch_transpose_pad(int kind, const double *in, void *out_hi, void 
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_float(const double *in, float *out, int64_t n, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    const int64_t blocks = (n + 255) / 256;
-    to_float_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(in, out, n);
+cudaError_t launch_epilogue_f32_inputs(const double *t1, const double *ovov, float *t1f, float *ovf, int o,
+                                       int v, int vp, cudaStream_t st) {
+    const int64_t n = (int64_t)o * o * vp * vp, blocks = (n + 255) / 256;
+    ovov_slabs_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(ovov, ovf, o, v, vp);
+    pad_rows_kernel<<<(unsigned)((o * (int64_t)vp + 255) / 256), 256, 0, st>>>(t1, t1f, o, v, vp);
     return cudaGetLastError();
 }
 

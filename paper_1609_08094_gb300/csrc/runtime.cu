@@ -245,13 +245,14 @@ void build_epilogue_inputs(Exec &ex, Problem &pb, const double *eps_occ, const d
         CK(cudaMemcpyAsync(pb.t1, t1, (size_t)o * v * sizeof(double), kd, ex.stream));
         CK(cudaMemcpyAsync(pb.ovov, ovov, nov2 * sizeof(double), kd, ex.stream));
     } else {
-        dalloc(ex, pb.t1, (size_t)o * v * sizeof(float));
-        dalloc(ex, pb.ovov, nov2 * sizeof(float));
+        const size_t vp = epi_vp(v);
+        dalloc(ex, pb.t1, (size_t)o * vp * sizeof(float));
+        dalloc(ex, pb.ovov, (size_t)o * o * vp * vp * sizeof(float));
         double *tmp1 = nullptr, *tmp2 = nullptr;
         const double *d1 = device_view(ex, t1, (size_t)o * v, host, tmp1);
-        CK(launch_to_float(d1, static_cast<float *>(pb.t1), (int64_t)o * v, ex.stream));
         const double *d2 = device_view(ex, ovov, nov2, host, tmp2);
-        CK(launch_to_float(d2, static_cast<float *>(pb.ovov), (int64_t)nov2, ex.stream));
+        CK(launch_epilogue_f32_inputs(d1, d2, static_cast<float *>(pb.t1), static_cast<float *>(pb.ovov), o, v,
+                                      (int)vp, ex.stream));
         free_tmp(ex, tmp1, (size_t)o * v);
         free_tmp(ex, tmp2, nov2);
         dalloc(ex, pb.dev_f, v * sizeof(float));
@@ -276,7 +277,8 @@ size_t problem_bytes(const Dims &d, int prec) {
     const size_t o = d.o, v = d.v, v2 = v * v;
     const size_t eb = elem_bytes(prec), parts = operand_planes(prec);
     size_t b = parts * eb * (o * v2 * d.dp + o * v2 * d.lp + o * o * v * d.dp + o * o * v * d.lp);
-    b += (o * o * v2 + o * v) * u_elem_bytes(prec) + (o + v) * 8 + v * 4;
+    const size_t ve = fp64_epilogue(prec) ? v : (size_t)epi_vp((int)v);  // FP32 inputs are padded
+    b += (o * o * ve * ve + o * ve) * u_elem_bytes(prec) + (o + v) * 8 + v * 4;
     const size_t nb = (v + EPI_TE - 1) / EPI_TE;
     b += nb * (nb + 1) * (nb + 2) / 6 * 12;
     b += o * (o + 1) * (o + 2) / 6 * 28;

@@ -12,6 +12,8 @@ namespace tcorr {
 namespace rt {
 
 constexpr int EPI_TE = 8;  // epilogue cube edge
+// padded virtual extent of the FP32 epilogue inputs (t1 rows, ovov slabs)
+inline int epi_vp(int v) { return (v + EPI_TE - 1) / EPI_TE * EPI_TE; }
 constexpr int TC_KB = 2;   // K chunks per tensor-core accumulator block (accuracy: see gemm_tc.cu)
 
 extern thread_local std::string g_create_error;

@@ -126,7 +126,9 @@ cudaError_t launch_transpose_pad(int kind, const double *in, void *out_hi, void 
                                  int64_t sb, int64_t sr, int64_t sc,
                                  int64_t ob, int64_t oc, double scale, cudaStream_t st);
 // out[n] = (float) in[n]
-cudaError_t launch_to_float(const double *in, float *out, int64_t n, cudaStream_t st);
+// FP32 epilogue inputs: t1 as [o][vp] and (p x | q z) as slabs [p][q][x][z] with x, z < vp, zero padded
+cudaError_t launch_epilogue_f32_inputs(const double *t1, const double *ovov, float *t1f, float *ovf, int o,
+                                       int v, int vp, cudaStream_t st);
 // dev_f[x] = (float)(eps_v[block_start(x)] - eps_v[x]), block edge te
 cudaError_t launch_block_deltas(const double *eps_v, float *dev_f, int v, int te, cudaStream_t st);
 // tasks[n] = (i, j, k): the sorted occupied triples i <= j <= k of o orbitals
