@@ -38,9 +38,9 @@ WORKLOAD = dict(o=50, v=450, naux=1500, seed=2)
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (152 SMs x 2070 MHz x 2 DFMA/clk x 2 flop)
 FP64_PROBE_TFLOPS = 1.20     # DFMA throughput probe on this machine's GB300
 # DRAM read+write bytes of one full-task launch of ugemm_f64_kernel at o=50,
-# v=450 from one ncu capture (profiles/ugemm_f64_kernel_o50_v450.md); valid
-# for this kernel version and workload only
-F64_GEMM_TRAFFIC_BYTES = {(50, 450): 5146864384 + 2179871488}
+# v=450 (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
+# this bench's FP64 leg); valid for this kernel version and workload only
+F64_GEMM_TRAFFIC_BYTES = {(50, 450): 5153704192 + 2181897216}
 # batched workload: n molecules, o ~ U{4..16}, v ~ U{20..120}, naux = 3(o+v),
 # per-molecule seeds seed+index; FP64 is timed on the first fp64_n of them
 # (the whole set is ~44 algorithmic TFLOP, ~40 s per pass on the FP64 pipe)
