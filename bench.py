@@ -667,8 +667,9 @@ def bench_mp2(args, rank, world, stream):
            "roofline": {"bound": "alu", "kernel": "mp2_pair_kernel", "achieved": fl / (kern_ms * 1e-3) / 1e12,
                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": fl / (kern_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
-                        "note": "achieved counts 2 v^2 naux flops per pair (tiles of 48 compute "
-                                "(ceil(v/48) 48)^2 / v^2 of that plus the diagonal tile pairs twice)"}}
+                        "note": "achieved counts 2 v^2 naux flops per pair; warps whose columns lie "
+                                "past v issue no FMA, so the only extra work is the padded rows of the "
+                                "last diagonal tile pair and naux rounded up to 8"}}
     if rank == 0 and not args.no_cpu:
         threads = oracle.max_threads()
         tc0 = time.time()

@@ -47,7 +47,7 @@ __device__ __forceinline__ int pick3(int a, int b, int c, int k) { return k == 0
 // and the E/O expansion of Z, as in the mixed epilogue), orbits with repeated
 // blocks the generic per-element form.
 template <typename UT, typename CT, int TE>
-__global__ void __launch_bounds__(NT) epilogue_kernel(const Wave wv) {
+__global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *Ws = reinterpret_cast<CT *>(smem_raw);
     constexpr int TP = TE + 1;               // padded innermost extent
@@ -153,28 +153,39 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const Wave wv) {
         // distinct blocks A < B < C: element orbits; slot q holds the element
         // with indices ordered as q (abc, acb, bac, bca, cab, cba); even slots
         // 0, 3, 4, odd 1, 2, 5; Z_q = 6 w_q + 2E - 4O (even) or 6 w_q + 2O - 4E (odd)
+        // thread: fixed (b, c), a = la0 and la0 + TE/2 (the TE^3 element orbits
+        // over NT = TE^3 / 2 threads); what depends only on b and c is read once
+        static_assert(NE == 2 * NT, "two element orbits per thread");
         const int A0 = ob0 * TE, B0 = ob1 * TE, C0 = ob2 * TE;
+        const int lb = (tid / TE) % TE, lc = tid % TE, la0 = tid / (TE * TE);
+        const int b = B0 + lb, c = C0 + lc;
         CT a4 = CT(0), a5 = CT(0);
-        for (int l = tid; l < NE; l += NT) {
-            const int la = l / (TE * TE), lb = (l / TE) % TE, lc = l % TE;
-            const int a = A0 + la, b = B0 + lb, c = C0 + lc;
-            if (a >= v || b >= v || c >= v) continue;
+        if (b < v && c < v) {
+        const CT tib = t1[ti * v + b], tic = t1[ti * v + c];
+        const CT tjb = t1[tj * v + b], tjc = t1[tj * v + c];
+        const CT tkb = t1[tkk * v + b], tkc = t1[tkk * v + c];
+        const CT jk_bc = ov_jk[b * ovs + c], jk_cb = ov_jk[c * ovs + b];
+        const CT ik_bc = ov_ik[b * ovs + c], ik_cb = ov_ik[c * ovs + b];
+        const CT ij_bc = ov_ij[b * ovs + c], ij_cb = ov_ij[c * ovs + b];
+        const CT ebc = eijk - p.eps_v[b] - p.eps_v[c];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int la = la0 + h * (TE / 2), a = A0 + la;
+            if (a >= v) break;  // a grows with h
             const CT w0 = Ws[0 * CUBE + (la * TE + lb) * TP + lc];
             const CT w1 = Ws[1 * CUBE + (la * TE + lc) * TP + lb];
             const CT w2 = Ws[2 * CUBE + (lb * TE + la) * TP + lc];
             const CT w3 = Ws[3 * CUBE + (lb * TE + lc) * TP + la];
             const CT w4 = Ws[4 * CUBE + (lc * TE + la) * TP + lb];
             const CT w5 = Ws[5 * CUBE + (lc * TE + lb) * TP + la];
-            const CT tia = t1[ti * v + a], tib = t1[ti * v + b], tic = t1[ti * v + c];
-            const CT tja = t1[tj * v + a], tjb = t1[tj * v + b], tjc = t1[tj * v + c];
-            const CT tka = t1[tkk * v + a], tkb = t1[tkk * v + b], tkc = t1[tkk * v + c];
-            // (j u | k w), (i u | k w), (i u | j w) over ordered pairs of {a, b, c}
-            const CT jk_bc = ov_jk[b * ovs + c], jk_cb = ov_jk[c * ovs + b], jk_ac = ov_jk[a * ovs + c];
-            const CT jk_ca = ov_jk[c * ovs + a], jk_ab = ov_jk[a * ovs + b], jk_ba = ov_jk[b * ovs + a];
-            const CT ik_bc = ov_ik[b * ovs + c], ik_cb = ov_ik[c * ovs + b], ik_ac = ov_ik[a * ovs + c];
-            const CT ik_ca = ov_ik[c * ovs + a], ik_ab = ov_ik[a * ovs + b], ik_ba = ov_ik[b * ovs + a];
-            const CT ij_bc = ov_ij[b * ovs + c], ij_cb = ov_ij[c * ovs + b], ij_ac = ov_ij[a * ovs + c];
-            const CT ij_ca = ov_ij[c * ovs + a], ij_ab = ov_ij[a * ovs + b], ij_ba = ov_ij[b * ovs + a];
+            const CT tia = t1[ti * v + a], tja = t1[tj * v + a], tka = t1[tkk * v + a];
+            // (j u | k w), (i u | k w), (i u | j w) over the ordered pairs of {a, b, c} that hold a
+            const CT jk_ac = ov_jk[a * ovs + c], jk_ca = ov_jk[c * ovs + a];
+            const CT jk_ab = ov_jk[a * ovs + b], jk_ba = ov_jk[b * ovs + a];
+            const CT ik_ac = ov_ik[a * ovs + c], ik_ca = ov_ik[c * ovs + a];
+            const CT ik_ab = ov_ik[a * ovs + b], ik_ba = ov_ik[b * ovs + a];
+            const CT ij_ac = ov_ij[a * ovs + c], ij_ca = ov_ij[c * ovs + a];
+            const CT ij_ab = ov_ij[a * ovs + b], ij_ba = ov_ij[b * ovs + a];
             // Y at each ordering q of (a,b,c): t^{q0}_i (j q1|k q2) + t^{q1}_j (i q0|k q2) + t^{q2}_k (i q0|j q1)
             const CT y0 = tia * jk_bc + tjb * ik_ac + tkc * ij_ab;
             const CT y1 = tia * jk_cb + tjc * ik_ab + tkb * ij_ac;
@@ -187,9 +198,10 @@ __global__ void __launch_bounds__(NT) epilogue_kernel(const Wave wv) {
             const CT wy = w0 * y0 + w1 * y1 + w2 * y2 + w3 * y3 + w4 * y4 + w5 * y5;
             const CT q4 = CT(6) * ww + CT(2) * (E * E + O * O) - CT(8) * E * O;
             const CT q5 = CT(6) * wy + (CT(2) * E - CT(4) * O) * (y0 + y3 + y4) + (CT(2) * O - CT(4) * E) * (y1 + y2 + y5);
-            const CT r = CT(1) / (eijk - p.eps_v[a] - p.eps_v[b] - p.eps_v[c]);
+            const CT r = CT(1) / (ebc - p.eps_v[a]);
             a4 += q4 * r;
             a5 += q5 * r;
+        }
         }
         kahan_add(s4, c4, double(a4));
         kahan_add(s5, c5, double(a5));

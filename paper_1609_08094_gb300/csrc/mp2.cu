@@ -15,9 +15,12 @@
 // memory instead of being computed.  Over A x B and B x A together the Coulomb part is 2 (G^2 + H^2)/eps
 // and the exchange part 2 G H / eps; a diagonal tile pair (A = B) covers its
 // block once, G^2 and G H.  The GEMM is a register-tiled DFMA loop (3 x 3
-// outputs of each of G and H per thread, K = naux in chunks of 8 staged
-// through double-buffered shared memory).  Per-CTA sums are reduced with a
-// deterministic Kahan pass.
+// outputs of each of G and H per thread: rows a = ta + 16 r, three
+// consecutive columns b = 3 tb + c; K = naux in chunks of 8 staged through
+// double-buffered shared memory).  A warp's six b columns are consecutive, so
+// on the ragged last tile the warps whose columns all lie past v issue no
+// FMA: the tile padding costs no FP64-pipe time.  Per-CTA sums are reduced
+// with a deterministic Kahan pass.
 #include <string.h>
 
 #include <algorithm>
@@ -101,13 +104,16 @@ __global__ void __launch_bounds__(MNT, 2) mp2_pair_kernel(const Mp2Args p) {
 
     const int nch = kp / MK;
     const bool diag = (A == B);  // H = G^T on a diagonal tile pair: computed from G below
+    // warp w holds the columns b = 6 w .. 6 w + 5 of tile B
+    const bool active = B * MT + 6 * (tid >> 5) < v;
     fetch(0);
     stash(0);
     __syncthreads();
     for (int ch = 0; ch < nch; ch++) {
         const int buf = ch & 1;
         if (ch + 1 < nch) fetch((ch + 1) * MK);
-        if (!diag) {
+        if (!active) {
+        } else if (!diag) {
 #pragma unroll
             for (int k = 0; k < MK; k++) {
                 double ai[3], bj[3], aj[3], bi[3];
@@ -115,8 +121,8 @@ __global__ void __launch_bounds__(MNT, 2) mp2_pair_kernel(const Mp2Args p) {
                 for (int r = 0; r < 3; r++) {
                     ai[r] = sm[buf][0][k][ta + 16 * r];
                     aj[r] = sm[buf][2][k][ta + 16 * r];
-                    bj[r] = sm[buf][1][k][tb + 16 * r];
-                    bi[r] = sm[buf][3][k][tb + 16 * r];
+                    bj[r] = sm[buf][1][k][3 * tb + r];
+                    bi[r] = sm[buf][3][k][3 * tb + r];
                 }
 #pragma unroll
                 for (int r = 0; r < 3; r++)
@@ -133,7 +139,7 @@ __global__ void __launch_bounds__(MNT, 2) mp2_pair_kernel(const Mp2Args p) {
 #pragma unroll
                 for (int r = 0; r < 3; r++) {
                     ai[r] = sm[buf][0][k][ta + 16 * r];
-                    bj[r] = sm[buf][1][k][tb + 16 * r];
+                    bj[r] = sm[buf][1][k][3 * tb + r];
                 }
 #pragma unroll
                 for (int r = 0; r < 3; r++)
@@ -149,12 +155,12 @@ __global__ void __launch_bounds__(MNT, 2) mp2_pair_kernel(const Mp2Args p) {
 #pragma unroll
         for (int r = 0; r < 3; r++)
 #pragma unroll
-            for (int c = 0; c < 3; c++) Gs[(ta + 16 * r) * MT + tb + 16 * c] = G[r][c];
+            for (int c = 0; c < 3; c++) Gs[(ta + 16 * r) * MT + 3 * tb + c] = G[r][c];
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < 3; r++)
 #pragma unroll
-            for (int c = 0; c < 3; c++) H[r][c] = Gs[(tb + 16 * c) * MT + ta + 16 * r];
+            for (int c = 0; c < 3; c++) H[r][c] = Gs[(3 * tb + c) * MT + ta + 16 * r];
     }
 
     // energy terms of this thread's (a, b)
@@ -167,7 +173,7 @@ __global__ void __launch_bounds__(MNT, 2) mp2_pair_kernel(const Mp2Args p) {
         const double ea = p.eps_v[a] - eij;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const int b = B * MT + tb + 16 * c;
+            const int b = B * MT + 3 * tb + c;
             if (b >= v) continue;
             const double rd = 1.0 / (ea + p.eps_v[b]);
             const double g = G[r][c], h = H[r][c];
