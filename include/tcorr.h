@@ -293,16 +293,23 @@ tcorr_status tcorr_server_destroy(tcorr_server_t s);
  *   g_aibj = sum_gamma C^gamma_ai C^gamma_bj           (Eqs. mp2_energy, eri_sym_decomp)
  *   eps^{ab}_{ij} = e_a + e_b - e_i - e_j                (Eq. e_orb_diff)
  *
- * evaluated over the occupied pairs i <= j (Eq. tasks_rimp2) in FP64 with the
- * ERI assembly and the energy fused in one kernel (g is never stored).
+ * evaluated over the occupied pairs i <= j (Eq. tasks_rimp2) with the ERI
+ * assembly and the energy fused in one kernel (g is never stored): in FP64
+ * on the FP64 pipe, or -- the paper's mixed-precision variant, re-designed --
+ * with the assembly on the sm_103 tensor cores in TF32 or BF16 hi + lo split
+ * precision (all four products: the lo*lo term is kept, as the same-index
+ * elements of i = j pairs are sums of squares; FP32 accumulation, FP32 energy
+ * terms, FP64 sums).
  *
  *   eps_occ [o], eps_vir [v], C [naux][v][o] = C^gamma_ai (row-major float64;
  *   device pointers, or host pointers with opts.host_inputs = 1; read only
  *   during tcorr_mp2_create).
  *
- * opts.prec must be TCORR_FP64 (EUNSUPPORTED otherwise); opts.profile times
- * the kernels (tcorr_mp2_kernel_times: class 1 = the fused pair kernel, 3 =
- * the final sum).  tcorr_mp2_energy writes e_out[3] = (E_J, E_K, E_MP2) with
+ * opts.prec: TCORR_FP64, TCORR_TF32X3 or TCORR_BF16X3 (EUNSUPPORTED for
+ * TCORR_FP64_OZ, and for the split precisions on a device other than sm_103);
+ * opts.profile times the kernels (tcorr_mp2_kernel_times: class 0 = layout
+ * prep, 1 = the fused pair kernel, 3 = the final sum).  The split-precision
+ * kernel's device waits are bounded: ETIMEOUT if one expires.  tcorr_mp2_energy writes e_out[3] = (E_J, E_K, E_MP2) with
  * E_J = -2 sum g^2/eps (Coulomb) and E_K = +sum g_aibj g_ajbi/eps (exchange).
  * Errors as for tcorr_create; create failures in tcorr_mp2_last_error(NULL).
  */

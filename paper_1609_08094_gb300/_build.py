@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_obj")
 LIB = os.path.join(HERE, "libtcorr.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["tcorr_api.cu", "runtime.cu", "prep.cu", "gemm_f64.cu", "epilogue.cu", "gemm_tc.cu", "noalloc.cu", "server.cu", "mp2.cu", "gemm_oz.cu"]
+SOURCES = ["tcorr_api.cu", "runtime.cu", "prep.cu", "gemm_f64.cu", "epilogue.cu", "gemm_tc.cu", "noalloc.cu", "server.cu", "mp2.cu", "gemm_oz.cu", "mp2_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", f"-I{INCLUDE}"]

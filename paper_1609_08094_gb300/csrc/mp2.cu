@@ -229,10 +229,14 @@ __global__ void __launch_bounds__(MNT) mp2_sum_kernel(const double *partials, in
 struct tcorr_mp2_s {
     Exec ex;
     int o = 0, v = 0, naux = 0, kp = 0, nt = 0, ntp = 0;
-    int64_t npair = 0, items = 0;
+    int64_t npair = 0, items = 0, nparts = 0;
     double *Ct = nullptr, *eps_o = nullptr, *eps_v = nullptr, *partials = nullptr, *d_out = nullptr;
     double *h_out = nullptr;
     int *pairs = nullptr, *tiles = nullptr;
+    // split precision (TF32X3 / BF16X3): hi and lo planes of C^T, FP32 eps_v, tensor maps
+    void *ct_hi = nullptr, *ct_lo = nullptr;
+    float *eps_vf = nullptr;
+    Mp2TcArgs tc{};
 };
 
 extern "C" {
@@ -255,8 +259,8 @@ tcorr_status tcorr_mp2_create(tcorr_mp2_t *out, int o, int v, int naux, const do
         const tcorr_status st = check_opts(op, g_create_error);
         if (st != TCORR_OK) return st;
     }
-    if (op.prec != TCORR_FP64) {
-        g_create_error = "RI-MP2 is implemented in FP64 only";
+    if (op.prec != TCORR_FP64 && op.prec != TCORR_TF32X3 && op.prec != TCORR_BF16X3) {
+        g_create_error = "RI-MP2 is implemented in FP64, TF32X3 and BF16X3";
         return TCORR_EUNSUPPORTED;
     }
     if (o > 4096 || v > 65536 || naux > (1 << 20) || (int64_t)o * v * naux > ((int64_t)1 << 36)) {
@@ -270,28 +274,41 @@ tcorr_status tcorr_mp2_create(tcorr_mp2_t *out, int o, int v, int naux, const do
     }
     Exec &ex = h->ex;
     try {
-        ex.stream = static_cast<cudaStream_t>(stream);
-        ex.profile = op.profile;
+        init_exec(ex, op, stream);  // SM count; split precision only on the sm_103 tensor cores
+        const bool split = op.prec != TCORR_FP64;
+        const int tile = split ? MP2_TC_TILE : MT;
         h->o = o;
         h->v = v;
         h->naux = naux;
-        h->kp = round_up(naux, MK);
-        h->nt = (v + MT - 1) / MT;
+        // K padded to whole 64-byte chunks of the tensor-core path (16 TF32 / 32 BF16
+        // values), or to the FP64 kernel's chunk
+        h->kp = round_up(naux, split ? 32 : MK);
+        h->nt = (v + tile - 1) / tile;
         h->ntp = h->nt * (h->nt + 1) / 2;
         h->npair = (int64_t)o * (o + 1) / 2;
         h->items = h->npair * h->ntp;
         if (h->items > 0x7fffffff) throw Fail{TCORR_EUNSUPPORTED, "too many work items"};
-        const size_t ct_bytes = (size_t)o * v * h->kp * sizeof(double);
+        // partials: one per item (FP64 kernel) or one per persistent CTA (tensor-core kernel)
+        h->nparts = split ? std::min<int64_t>(ex.sm_count, h->items) : h->items;
+        const size_t ct_bytes = (size_t)o * v * h->kp * elem_bytes(op.prec) * (split ? 2 : 1);  // hi + lo
         size_t free_b = 0, total_b = 0;
         CK(cudaMemGetInfo(&free_b, &total_b));
-        const size_t need = ct_bytes + (size_t)h->items * 16 + (op.host_inputs ? (size_t)o * v * naux * 8 : 0) +
+        const size_t need = ct_bytes + (size_t)h->nparts * 16 + (op.host_inputs ? (size_t)o * v * naux * 8 : 0) +
                             ((size_t)64 << 20);
         if (need > free_b)
             throw Fail{TCORR_ENOMEM, "footprint " + std::to_string(need) + " bytes exceeds free device memory"};
-        dalloc(ex, h->Ct, ct_bytes);
+        if (split) {
+            const size_t plane = ct_bytes / 2;
+            dalloc(ex, h->ct_hi, plane);
+            dalloc(ex, h->ct_lo, plane);
+            dalloc(ex, h->eps_vf, (size_t)v * sizeof(float));
+            alloc_common(ex);  // device error flag of the bounded waits
+        } else {
+            dalloc(ex, h->Ct, ct_bytes);
+        }
         dalloc(ex, h->eps_o, (size_t)o * sizeof(double));
         dalloc(ex, h->eps_v, (size_t)v * sizeof(double));
-        dalloc(ex, h->partials, (size_t)h->items * 2 * sizeof(double));
+        dalloc(ex, h->partials, (size_t)h->nparts * 2 * sizeof(double));
         dalloc(ex, h->d_out, 3 * sizeof(double));
         halloc(ex, h->h_out, 3 * sizeof(double));
         const bool host = op.host_inputs == 1;
@@ -300,13 +317,22 @@ tcorr_status tcorr_mp2_create(tcorr_mp2_t *out, int o, int v, int naux, const do
         CK(cudaMemcpyAsync(h->eps_v, eps_vir, (size_t)v * sizeof(double), kd, ex.stream));
         double *tmp = nullptr;
         const double *dC = device_view(ex, C, (size_t)o * v * naux, host, tmp);
-        {   // Ct[i][a][gamma] = C[gamma][a][i], gamma padded to kp with zeros
+        {   // Ct[i][a][gamma] = C[gamma][a][i], gamma padded to kp with zeros (split:
+            // hi and lo planes in TF32 or BF16)
             Timer tm(ex, KC_PREP);
-            CK(launch_transpose_pad(0, dC, h->Ct, nullptr, o, naux, h->kp, v, 1, (int64_t)v * o, o,
-                                    (int64_t)v * h->kp, h->kp, 1.0, ex.stream));
+            const int kind = op.prec == TCORR_TF32X3 ? 1 : (op.prec == TCORR_BF16X3 ? 2 : 0);
+            CK(launch_transpose_pad(kind, dC, split ? h->ct_hi : h->Ct, split ? h->ct_lo : nullptr, o, naux, h->kp,
+                                    v, 1, (int64_t)v * o, o, (int64_t)v * h->kp, h->kp, 1.0, ex.stream));
             tm.stop();
         }
         free_tmp(ex, tmp, (size_t)o * v * naux);
+        if (split) {  // FP32 copy of the virtual energies for the FP32 denominators
+            std::vector<double> ev(v);
+            CK(cudaMemcpyAsync(ev.data(), h->eps_v, (size_t)v * sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
+            CK(cudaStreamSynchronize(ex.stream));
+            std::vector<float> evf(ev.begin(), ev.end());
+            CK(cudaMemcpy(h->eps_vf, evf.data(), (size_t)v * sizeof(float), cudaMemcpyHostToDevice));
+        }
         std::vector<int> pr, tl;
         for (int i = 0; i < o; i++)
             for (int j = i; j < o; j++) { pr.push_back(i); pr.push_back(j); }
@@ -316,6 +342,22 @@ tcorr_status tcorr_mp2_create(tcorr_mp2_t *out, int o, int v, int naux, const do
         dalloc(ex, h->tiles, tl.size() * sizeof(int));
         CK(cudaMemcpy(h->pairs, pr.data(), pr.size() * sizeof(int), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(h->tiles, tl.data(), tl.size() * sizeof(int), cudaMemcpyHostToDevice));
+        if (split) {
+            Mp2TcArgs &a = h->tc;
+            a.pairs = h->pairs;
+            a.tiles = h->tiles;
+            a.eps_o = h->eps_o;
+            a.eps_v = h->eps_v;
+            a.eps_vf = h->eps_vf;
+            a.partials = h->partials;
+            a.err = ex.err;
+            a.v = v;
+            a.ntp = h->ntp;
+            a.items = h->items;
+            std::string err;
+            if (mp2_tc_fill(a, op.prec, h->ct_hi, h->ct_lo, o, v, h->kp, err) != cudaSuccess)
+                throw Fail{TCORR_ECUDA, err};
+        }
         CK(cudaStreamSynchronize(ex.stream));
         resolve_timers(ex);
     } catch (const Fail &f) {
@@ -344,22 +386,27 @@ tcorr_status tcorr_mp2_energy(tcorr_mp2_t h, double *e_out) {
         return TCORR_EINVAL;
     }
     try {
-        Mp2Args a{h->Ct, h->eps_o, h->eps_v, h->pairs, h->tiles, h->v, h->kp, h->ntp, h->partials};
         {
             Timer tm(ex, KC_GEMM);
-            mp2_pair_kernel<<<(unsigned)h->items, MNT, 0, ex.stream>>>(a);
-            CK(cudaGetLastError());
+            if (ex.prec == TCORR_FP64) {
+                Mp2Args a{h->Ct, h->eps_o, h->eps_v, h->pairs, h->tiles, h->v, h->kp, h->ntp, h->partials};
+                mp2_pair_kernel<<<(unsigned)h->items, MNT, 0, ex.stream>>>(a);
+                CK(cudaGetLastError());
+            } else {
+                CK(launch_mp2_tc(ex.prec, ex.sm_count, h->tc, ex.stream));
+            }
             tm.stop();
         }
         {
             Timer tm(ex, KC_RED);
-            mp2_sum_kernel<<<1, MNT, 0, ex.stream>>>(h->partials, h->items, h->d_out);
+            mp2_sum_kernel<<<1, MNT, 0, ex.stream>>>(h->partials, h->nparts, h->d_out);
             CK(cudaGetLastError());
             tm.stop();
         }
         CK(cudaMemcpyAsync(h->h_out, h->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
         CK(cudaStreamSynchronize(ex.stream));
         resolve_timers(ex);
+        if (ex.prec != TCORR_FP64) check_err_flag(ex);
         for (int c = 0; c < 3; c++) e_out[c] = h->h_out[c];
     } catch (const Fail &f) {
         ex.last_error = f.msg;

@@ -181,4 +181,23 @@ cudaError_t oz_prepare();
 cudaError_t launch_ugemm_oz(int sm_count, const Wave &w, cudaStream_t st);
 cudaError_t launch_ugemm_tc(int prec, int sm_count, const Wave &w, cudaStream_t st);
 
+// ---- RI-MP2 in split precision on the tensor cores (mp2_tc.cu) ------------------
+constexpr int MP2_TC_TILE = 128;  // virtual indices per tile (M = N of the MMAs)
+struct Mp2TcArgs {
+    CUtensorMap map[2];       // hi, lo planes of C^T as [o][v][kp] (K-major), box {chunk, 128, 1}
+    const int *pairs;         // [npair][2], i <= j
+    const int *tiles;         // [ntp][2], A <= B (tiles of MP2_TC_TILE)
+    const double *eps_o, *eps_v;
+    const float *eps_vf;      // eps_v rounded to FP32
+    double *partials;         // [grid][2]: (E_J, E_K) of each CTA, pair weights applied
+    int *err;                 // DERR_* flags of bounded waits that expired
+    int v, nch, ntp;          // nch: K chunks of 64 bytes (set by mp2_tc_fill)
+    int64_t items;            // npair * ntp
+};
+// Encodes the two operand maps of the planes hi / lo ([o][v][kp], TF32 or BF16)
+// and sets a.nch; kp must be a multiple of the chunk (16 TF32, 32 BF16 values).
+cudaError_t mp2_tc_fill(Mp2TcArgs &a, int prec, void *hi, void *lo, int o, int v, int kp, std::string &err);
+// One persistent CTA per SM (at most items); writes min(sm_count, items) partial pairs.
+cudaError_t launch_mp2_tc(int prec, int sm_count, const Mp2TcArgs &a, cudaStream_t st);
+
 }  // namespace tcorr

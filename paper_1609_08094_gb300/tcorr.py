@@ -483,7 +483,8 @@ class Server:
 class Mp2:
     """RI-MP2 correlation energy of one problem (tcorr_mp2_*): eps_occ [o],
     eps_vir [v], C [naux][v][o] (all CUDA tensors, or all numpy arrays which
-    are copied in).  ``energy()`` returns (E_J, E_K, E_MP2); FP64 only."""
+    are copied in).  ``energy()`` returns (E_J, E_K, E_MP2); prec "fp64",
+    "tf32x3" or "bf16x3" (the split precisions on the tensor cores)."""
 
     def __init__(self, o, v, naux, eps_occ, eps_vir, C, profile=False, stream=None, prec="fp64"):
         lib = load()

@@ -1,7 +1,9 @@
 """RI-MP2 (Sec. 2.1) on the GPU against the oracle, through the C ABI.
-Tolerance 1e-10 relative (FP64 path): tile edges of 48 virtual indices, so
+FP64 path, tolerance 1e-10 relative: tile edges of 48 virtual indices, so
 the shapes below span several tiles with ragged tails, plus o = 1, v below
-one tile, naux below one K chunk, host inputs and determinism."""
+one tile, naux below one K chunk, host inputs and determinism.  Split
+precision on the tensor cores (TF32x3, BF16x3), tolerance 1e-6 relative:
+tiles of 128 with ragged tails, one pair, ragged naux, host inputs."""
 import numpy as np
 import pytest
 import torch
@@ -62,8 +64,62 @@ def test_mp2_same_system_as_the_triples_generator():
         assert rel(m.energy()[2], e_ref) <= 1e-10
 
 
-def test_mp2_rejects_mixed_precision():
+def test_mp2_rejects_fp64_emulation():
     inst = synth.make_mp2_instance(2, 10, 4, 1).to("cuda")
     with pytest.raises(tcorr.TcorrError) as ex:
-        tcorr.Mp2.from_instance(inst, prec="bf16x3")
+        tcorr.Mp2.from_instance(inst, prec="fp64_oz")
     assert ex.value.status == 5
+
+
+MIXED_TOL = 1e-6
+
+
+def split_tol(prec, o, v, naux):
+    """1e-6 relative, except BF16x3 on problems of fewer than 1e5 (pair, a, b,
+    gamma) terms.  A BF16 hi + lo split leaves a residual of up to 2^-18 of
+    each operand (lo is rounded to 8 significant bits), so an element of g
+    can be off by 2 x 2^-18 of its terms' magnitude and E, quadratic in g, by
+    about twice that: 2^-15 in the worst case.  The 1e-6 level relies on the
+    residuals' random signs averaging over many terms, which a single pair
+    with v = 13 and naux = 7 does not give."""
+    if prec == "bf16x3" and o * (o + 1) // 2 * v * v * naux < 10 ** 5:
+        return 2.0 ** -15
+    return MIXED_TOL
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("o,v,naux,seed", [
+    (3, 20, 5, 1),         # one tile of 128 with 20 valid rows; naux below one K chunk
+    (1, 13, 7, 3),         # a single pair (i = j)
+    (4, 130, 61, 4),       # two tiles, the second with 2 valid rows
+    (7, 200, 200, 5),      # ragged naux (kp = 224)
+    (2, 300, 420, 7),      # three tiles, the last with 44 valid rows
+])
+def test_mp2_split_precision_matches_oracle(prec, o, v, naux, seed):
+    """Tensor-core RI-MP2 (the paper's mixed-precision variant, split precision)
+    against the FP64 oracle at 1e-6 relative, deterministic."""
+    inst = synth.make_mp2_instance(o, v, naux, seed)
+    ref = oracle.mp2_energy(inst)
+    with tcorr.Mp2.from_instance(inst.to("cuda"), prec=prec) as m:
+        e1 = m.energy()
+        e2 = m.energy()
+    assert e1 == e2
+    err = rel(e1[2], ref[2])
+    print(f"rimp2 {prec} o={o} v={v} naux={naux}: rel err E {err:.2e}, E_J {rel(e1[0], ref[0]):.2e}, "
+          f"E_K {abs(e1[1] - ref[1]) / abs(ref[2]):.2e}")
+    tol = split_tol(prec, o, v, naux)
+    assert err <= tol
+    assert rel(e1[0], ref[0]) <= tol
+    assert abs(e1[1] - ref[1]) <= tol * abs(ref[2])
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_mp2_split_precision_host_inputs_and_profile(prec):
+    inst = synth.make_mp2_instance(5, 140, 90, 11)
+    with tcorr.Mp2.from_instance(inst, prec=prec, profile=True) as m:    # numpy: copied in
+        e_host = m.energy()
+        kt = m.kernel_times()
+    with tcorr.Mp2.from_instance(inst.to("cuda"), prec=prec) as m:
+        e_dev = m.energy()
+    assert e_host == e_dev
+    assert kt["gemm"][1] == 1 and kt["gemm"][0] > 0
