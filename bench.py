@@ -632,7 +632,9 @@ def bench_mp2(args, rank, world, stream):
     """RI-MP2 (Sec. 2.1) of the same synthetic system as the main workload
     (its occupied-virtual factors as fitting coefficients), FP64: device time
     of the fused pair kernel over all i <= j pairs per step, the oracle on the
-    host cores over the whole problem, and their agreement."""
+    host cores over the whole problem, and their agreement; then the
+    mixed-precision variant (TF32x3, BF16x3 on the tensor cores) with its
+    error against the FP64 energy."""
     import numpy as np
     import torch
 
