@@ -18,9 +18,9 @@
 // then acts on the smallest partial sums).  Unlike the (T) contractions the
 // lo*lo product is kept: for i = j the same-index elements g_aa are sums of
 // squares, where the dropped lo^2 would bias g one-signedly by the mean
-// square of the split's relative residual (~1e-6 with BF16, most of E for
-// small o); the kernel is bound by operand ingest, so the fourth product
-// costs no time.  The epilogue warps fold every block into register totals
+// square of the split's relative residual (~3e-6 with BF16; those elements
+// carry most of E for small o); the kernel is bound by operand ingest, so
+// the fourth product costs no time.  The epilogue warps fold every block into register totals
 // with round-to-nearest FP32 adds, and at the end of the item form the energy
 // terms of their (a, b): over A x B and B x A together -2 (g^2 + h^2) / eps and
 // 2 g h / eps; a diagonal tile pair covers its block once, -2 g^2 / eps and
