@@ -128,3 +128,28 @@ def test_server_arguments_rejected_before_device_work(lib):
     assert lib.tcorr_server_drain(None) == 1
     assert lib.tcorr_server_stats(None, None) == 1
     assert lib.tcorr_server_destroy(None) == 0
+
+
+def test_mp2_arguments_rejected_before_device_work(lib):
+    h = ctypes.c_void_p()
+    one = (ctypes.c_double * 1)()
+    p = ctypes.cast(one, ctypes.c_void_p)
+    # NULL out, sizes < 1, NULL arrays: EINVAL
+    assert lib.tcorr_mp2_create(None, 2, 2, 2, p, p, p, None, None) == 1
+    assert lib.tcorr_mp2_create(ctypes.byref(h), 0, 2, 2, p, p, p, None, None) == 1
+    assert lib.tcorr_mp2_create(ctypes.byref(h), 2, 0, 2, p, p, p, None, None) == 1
+    assert lib.tcorr_mp2_create(ctypes.byref(h), 2, 2, 0, p, p, p, None, None) == 1
+    assert lib.tcorr_mp2_create(ctypes.byref(h), 2, 2, 2, p, p, None, None, None) == 1
+    # an unknown precision is EINVAL; FP64 emulation is not an RI-MP2 precision: EUNSUPPORTED
+    bad = tcorr.Opts(prec=7)
+    assert lib.tcorr_mp2_create(ctypes.byref(h), 2, 2, 2, p, p, p, ctypes.byref(bad), None) == 1
+    oz = tcorr.Opts(prec=tcorr.PREC["fp64_oz"])
+    assert lib.tcorr_mp2_create(ctypes.byref(h), 2, 2, 2, p, p, p, ctypes.byref(oz), None) == 5
+    assert b"TF32X3" in lib.tcorr_mp2_last_error(None)
+    assert h.value is None
+    # calls on a NULL handle
+    e = (ctypes.c_double * 3)()
+    assert lib.tcorr_mp2_energy(None, e) == 1
+    assert lib.tcorr_mp2_kernel_times(None, None, None, 0) == 1
+    assert lib.tcorr_mp2_device_bytes(None) == -1
+    assert lib.tcorr_mp2_destroy(None) == 0
