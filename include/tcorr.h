@@ -80,7 +80,10 @@ typedef struct {
 } tcorr_opts;           /* zero-initialised = defaults */
 
 /*
- * Create a handle for one (T) problem with o occupied and v virtual orbitals.
+ * Create a handle for one (T) problem with o occupied and v virtual orbitals:
+ * the inputs of the operation above (Sec. 2.2), which the handle re-lays out
+ * for the W contractions of Eq. analytical_triples_ampl and the energy terms
+ * of Eqs. piecuch_4th_order, piecuch_5th_order.
  *
  *   eps_occ [o]           orbital energies e_i
  *   eps_vir [v]           orbital energies e_a
@@ -116,9 +119,10 @@ int64_t tcorr_num_tasks(tcorr_t h);
 tcorr_status tcorr_task(tcorr_t h, int64_t idx, int *ijk);
 
 /*
- * Full energy.  e_out (host, 3 doubles) receives E[4], E[5], E(T).
- * Synchronous on the handle's stream.  Deterministic: the same handle
- * returns bit-identical results.
+ * Full energy: E[4], E[5] (Eqs. piecuch_4th_order, piecuch_5th_order) and
+ * E(T) summed over every task of the restricted loop (Sec. 3).  e_out (host,
+ * 3 doubles) receives E[4], E[5], E(T).  Synchronous on the handle's stream.
+ * Deterministic: the same handle returns bit-identical results.
  */
 tcorr_status tcorr_energy(tcorr_t h, double *e_out);
 
@@ -212,7 +216,9 @@ const char *tcorr_batch_last_error(tcorr_batch_t b);
 tcorr_status tcorr_batch_destroy(tcorr_batch_t b);
 
 /*
- * Server: continuous batching of (T) jobs that arrive over time.
+ * Server: continuous batching of (T) jobs that arrive over time (each job
+ * the operation above; its tasks are the restricted loop of Sec. 3, of equal
+ * weight, Sec. 5, so tasks of different jobs can share a wave).
  *
  * Jobs are submitted at any time and queue in arrival order.  Each
  * tcorr_server_step admits queued jobs, in order, while their device
