@@ -160,6 +160,16 @@ SERVER_STATS = ("submitted", "done", "failed", "running", "queued", "bytes", "pe
 NOALLOC_MAX_V = 64
 
 
+def _prec(prec) -> int:
+    """tcorr_precision of a name ('fp64', 'tf32x3', 'bf16x3', 'fp64_oz') or an int."""
+    if isinstance(prec, str):
+        key = prec.lower()
+        if key not in PREC:
+            raise ValueError(f"unknown precision {prec!r}; one of {sorted(PREC)}")
+        return PREC[key]
+    return int(prec)
+
+
 def _shape_check(name, a, shape):
     if tuple(a.shape) != tuple(shape):
         raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(a.shape)}")
@@ -185,8 +195,8 @@ class Tcorr:
     """One (T) problem resident on the GPU.
 
     Inputs are the seven arrays of tcorr_create (torch CUDA tensors, or all
-    numpy / CPU arrays, which are copied in).  ``prec`` is 'fp64', 'tf32x3' or
-    'bf16x3'.  ``stream``: a torch.cuda.Stream, an integer cudaStream_t, or
+    numpy / CPU arrays, which are copied in).  ``prec`` is 'fp64', 'fp64_oz',
+    'tf32x3' or 'bf16x3'.  ``stream``: a torch.cuda.Stream, an integer cudaStream_t, or
     None for torch's current stream (device inputs) / the default stream."""
 
     def __init__(self, o, v, eps_occ, eps_vir, t1, t2, vvvo, ooov, ovov, prec="fp64",
@@ -201,8 +211,7 @@ class Tcorr:
         for k, a in arrays.items():
             _shape_check(k, a, shapes[k])
             ptrs.append(_pointer(k, a, on_device))
-        if isinstance(prec, str):
-            prec = PREC[prec.lower()]
+        prec = _prec(prec)
         opts = Opts(prec=int(prec), host_inputs=0 if on_device else 1,
                     batch_tasks=int(batch_tasks), profile=1 if profile else 0,
                     test_stall=1 if test_stall else 0, tune=1 if tune else 0)
@@ -316,8 +325,7 @@ class Batch:
                 ptrs.append(_pointer(f"problem {n} {name}", a, on_device))
                 keep.append(a)
             arr[n] = Problem(o, v, *ptrs)
-        if isinstance(prec, str):
-            prec = PREC[prec.lower()]
+        prec = _prec(prec)
         opts = Opts(prec=int(prec), host_inputs=0 if on_device else 1,
                     batch_tasks=int(batch_tasks), profile=1 if profile else 0,
                     tune=1 if tune else 0, eager=1 if eager else 0, wave_mb=int(wave_mb))
@@ -396,8 +404,7 @@ class Server:
     def __init__(self, prec="bf16x3", hbm_bytes=0, wave_mb=0, batch_tasks=0, profile=False,
                  stream=None, test_stall=False):
         lib = load()
-        if isinstance(prec, str):
-            prec = PREC[prec.lower()]
+        prec = _prec(prec)
         opts = Opts(prec=int(prec), host_inputs=0, batch_tasks=int(batch_tasks),
                     profile=1 if profile else 0, test_stall=1 if test_stall else 0,
                     wave_mb=int(wave_mb))
@@ -494,8 +501,7 @@ class Mp2:
         for name, a in (("eps_occ", eps_occ), ("eps_vir", eps_vir), ("C", C)):
             _shape_check(name, a, shapes[name])
             ptrs.append(_pointer(name, a, on_device))
-        if isinstance(prec, str):
-            prec = PREC[prec.lower()]
+        prec = _prec(prec)
         opts = Opts(prec=int(prec), host_inputs=0 if on_device else 1, profile=1 if profile else 0)
         if stream is None and on_device:
             import torch
