@@ -5,7 +5,6 @@ that arrive while it runs (its work units do the same arithmetic whatever
 shares a wave), equal to a single handle's, and within tolerance of the
 oracle; admission must respect the memory budget; an expired device wait
 must fail the running jobs with TCORR_ETIMEOUT and leave the server usable."""
-import numpy as np
 import pytest
 import torch
 
