@@ -42,6 +42,14 @@ __device__ __forceinline__ int perm_pos(int s, int d) {
 }
 __device__ __forceinline__ int pick3(int a, int b, int c, int k) { return k == 0 ? a : (k == 1 ? b : c); }
 
+// 1/d in FP64 from an FP32 estimate r0 of it (relative error e, |e| < 1e-6):
+// one Newton-Raphson step for the root of f(r) = 1/r - d, r1 = r0 + r0 (1 - d r0),
+// leaves a relative error of e^2 plus FP64 rounding.
+__device__ __forceinline__ double recip64(double d, float r0) {
+    const double r = (double)r0;
+    return fma(r, fma(-d, r, 1.0), r);
+}
+
 // FP64 epilogue; TE: cube edge.  Orbits of three distinct blocks take the
 // element-orbit form (the six orderings of one (a,b,c) share one denominator
 // and the E/O expansion of Z, as in the mixed epilogue), orbits with repeated
@@ -251,19 +259,31 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
 
 #undef OBP
 
-// Mixed-precision epilogue: the same block-orbit algorithm with 8^3 cubes in
-// FP32, sized for occupancy (about 20 KB of shared memory, 48 registers: 5
-// CTAs per SM).  The U loads of a thread are issued first, right after the
-// orbit's block indices are read, and consumed after the Y operands have been
-// staged, so their latency overlaps the staging.
-// The Y operands of the orbit (t1 rows and the three ovov sub-blocks) and
-// the block-relative virtual energies are staged in shared memory.  The
-// denominator of element (x,y,z) is base + d[x] + d[y] + d[z] with
-// base = e_i+e_j+e_k - e_A0 - e_B0 - e_C0 formed in FP64 once per CTA (it is
-// the same for all six cubes of an orbit) and rounded to FP32 once, and
-// d[x] = e_X0 - e_x the FP32 offset from x's block origin.  Element terms
-// are summed in FP32 per thread, warp and CTA (round to nearest); the orbit
-// partials of a task are summed in FP64 (Kahan) by the task reduction.
+// Mixed-precision epilogue: the same block-orbit algorithm with 8^3 cubes of
+// FP32 W (the tensor-core contractions' output), sized for occupancy (about
+// 20 KB of shared memory, 5 CTAs per SM).  The U loads of a thread are issued
+// first, right after the orbit's block indices are read, and consumed after
+// the Y operands have been staged, so their latency overlaps the staging.
+// The Y operands of the orbit (t1 rows and the three ovov sub-blocks) are
+// staged in shared memory, with the orbit's virtual energies in FP64 and as
+// FP32 offsets from their block origins.
+//
+// Precision of the energy terms (the numerators are FP32, everything from the
+// denominator on is FP64):
+//  - the element-orbit numerators sum_q Z_q W_q and sum_q Z_q Y_q (six
+//    orderings of one (a,b,c), or one element of an orbit with repeated
+//    blocks) are formed in FP32 from the FP32 W, Y;
+//  - the denominator D = e_i+e_j+e_k - e_a - e_b - e_c is formed in FP64;
+//  - 1/D: an FP32 reciprocal of the FP32 denominator (block base + offsets,
+//    relative error about 1e-7) refined by one Newton-Raphson step
+//    r <- r + r (1 - D r) in FP64 against the FP64 D, which squares the
+//    relative error (below 1e-13);
+//  - numerator x 1/D and every sum from there on (per thread, warp shuffles,
+//    CTA) in FP64; the orbit partials of a task are summed in FP64 (Kahan)
+//    by the task reduction.
+// One Newton step costs two FP64 FMAs per element orbit (per element in the
+// orbits with repeated blocks), so the FP64 pipe (1/64 of the FP32 rate on
+// this part) sees about one instruction per element.
 constexpr int F8 = 8;
 constexpr int FP0 = 69, FP1 = 8;    // plane / row pitch of a cube: at most 2-way bank conflicts
 constexpr int FSLOT = F8 * FP0;     // floats per cube slot
@@ -275,11 +295,13 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
     __shared__ float Ws[6 * FSLOT];
     __shared__ float T1s[3][3][F8];          // [occupied i,j,k][orbit block][local]
     __shared__ __align__(16) float OVs[3][3][3][F8 * F8];  // [(jk),(ik),(ij)][block][block][8x8]
-    __shared__ float Dls[3][F8];             // [orbit block][local] block-relative energies
+    __shared__ float Dls[3][F8];             // [orbit block][local] block-relative energies (FP32 seed)
+    __shared__ double Evs[3][F8];            // [orbit block][local] virtual energies (FP64)
     __shared__ float base_s;
+    __shared__ double eijk_s;
     __shared__ int comp[6][6];
     __shared__ int distinct[6];
-    __shared__ float red[NT / 32][2];
+    __shared__ double red[NT / 32][2];
 
     const int64_t item = blockIdx.x;
     const Seg sg = wv.segs[seg_find(wv.segs, wv.nseg, item, [](const Seg &x) { return x.epi0; })];
@@ -342,6 +364,7 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
     if (tid == 96) {
         const double eijk = p.eps_o[ti] + p.eps_o[tj] + p.eps_o[tkk];
         base_s = (float)(eijk - p.eps_v[ob0 * F8] - p.eps_v[ob1 * F8] - p.eps_v[ob2 * F8]);
+        eijk_s = eijk;
     }
     // stage t1, ovov sub-blocks and block-relative energies.  The FP32 inputs
     // are zero padded to vp (t1 rows [p][x], ovov slabs [p][q][x][z]): every
@@ -356,6 +379,7 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
     } else if (tid >= 96 + 32 && tid < 96 + 32 + 3 * F8) {
         const int e = tid - 128, b = e / F8, m = e % F8, x = pick3(ob0, ob1, ob2, b) * F8 + m;
         Dls[b][m] = x < v ? p.dev_f[x] : 0.f;
+        Evs[b][m] = x < v ? p.eps_v[x] : 0.0;
     }
     // slices: 0 = (j y | k z), 1 = (i x | k z), 2 = (i x | j y); 3 x 9 sub-blocks
     // x 8 rows x 2 halves = 432 float4
@@ -393,7 +417,8 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
     __syncthreads();
 
     const float base = base_s;
-    float a4 = 0.f, a5 = 0.f;
+    const double eijk = eijk_s;
+    double a4 = 0.0, a5 = 0.0;
     if (ob0 < ob1 && ob1 < ob2) {
         // Distinct blocks: each thread takes element orbits, the six orderings
         // of one (a,b,c) with a in A, b in B, c in C.  Slot q holds the element
@@ -414,6 +439,7 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
         const float ik_bc = OVV(1, 1, 2, lb, lc), ik_cb = OVV(1, 2, 1, lc, lb);
         const float ij_bc = OVV(2, 1, 2, lb, lc), ij_cb = OVV(2, 2, 1, lc, lb);
         const float dbc = base + (Dls[1][lb] + Dls[2][lc]);
+        const double dbc64 = eijk - Evs[1][lb] - Evs[2][lc];
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int la = la0 + 4 * h;
@@ -445,9 +471,9 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
             const float wy = w0 * y0 + w1 * y1 + w2 * y2 + w3 * y3 + w4 * y4 + w5 * y5;
             const float s4 = 6.f * ww + 2.f * (E * E + O * O) - 8.f * E * O;
             const float s5 = 6.f * wy + (2.f * E - 4.f * O) * (y0 + y3 + y4) + (2.f * O - 4.f * E) * (y1 + y2 + y5);
-            const float r = __fdividef(1.f, dbc + Dls[0][la]);
-            a4 = fmaf(s4, r, a4);
-            a5 = fmaf(s5, r, a5);
+            const double r = recip64(dbc64 - Evs[0][la], __fdividef(1.f, dbc + Dls[0][la]));
+            a4 = fma((double)s4, r, a4);
+            a5 = fma((double)s5, r, a5);
         }
 #undef OVV
     } else {
@@ -472,9 +498,10 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
                 const float yv = T1s[0][p0][l0] * OVs[0][p1][p2][l1 * F8 + l2] +
                                  T1s[1][p1][l1] * OVs[1][p0][p2][l0 * F8 + l2] +
                                  T1s[2][p2][l2] * OVs[2][p0][p1][l0 * F8 + l1];
-                const float r = __fdividef(1.f, base + (Dls[p0][l0] + Dls[p1][l1] + Dls[p2][l2]));
-                a4 = fmaf(zv * w0, r, a4);
-                a5 = fmaf(zv * yv, r, a5);
+                const double r = recip64(eijk - Evs[p0][l0] - Evs[p1][l1] - Evs[p2][l2],
+                                         __fdividef(1.f, base + (Dls[p0][l0] + Dls[p1][l1] + Dls[p2][l2])));
+                a4 = fma((double)(zv * w0), r, a4);
+                a5 = fma((double)(zv * yv), r, a5);
             }
         }
     }
@@ -482,20 +509,16 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
         a4 += __shfl_xor_sync(0xffffffffu, a4, off);
         a5 += __shfl_xor_sync(0xffffffffu, a5, off);
     }
-    // cross-warp sum in FP32 (8 terms, round to nearest); the orbit partials are
+    // cross-warp sum in FP64 (8 terms, fixed order); the orbit partials are
     // summed in FP64 (Kahan) per task
     if ((tid & 31) == 0) { red[tid >> 5][0] = a4; red[tid >> 5][1] = a5; }
     __syncthreads();
-    if (tid < 32) {
-        float b4 = tid < NT / 32 ? red[tid][0] : 0.f, b5 = tid < NT / 32 ? red[tid][1] : 0.f;
-        for (int off = 4; off > 0; off >>= 1) {
-            b4 += __shfl_xor_sync(0xffffffffu, b4, off);
-            b5 += __shfl_xor_sync(0xffffffffu, b5, off);
-        }
-        if (tid == 0) {
-            out[0] = (double)b4;
-            out[1] = (double)b5;
-        }
+    if (tid == 0) {
+        double b4 = 0.0, b5 = 0.0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; w++) { b4 += red[w][0]; b5 += red[w][1]; }
+        out[0] = b4;
+        out[1] = b5;
     }
 }
 #undef OBP
