@@ -43,13 +43,14 @@ FP64_PROBE_TFLOPS = 1.20     # DFMA throughput probe on this machine's GB300
 F64_GEMM_TRAFFIC_BYTES = {(50, 450): 5153704192 + 2181897216}
 # batched workload: n molecules, o ~ U{4..16}, v ~ U{20..120}, naux = 3(o+v),
 # per-molecule seeds seed+index; FP64 is timed on the first fp64_n of them
-# (the whole set is ~44 algorithmic TFLOP, ~40 s per pass on the FP64 pipe)
-BATCH = dict(n=256, seed=4, fp64_n=32)
+# (the whole set is ~44 algorithmic TFLOP, ~40 s per pass on the FP64 pipe);
+# kernel shares and the unbatched FP64 comparison use the first prof_n
+BATCH = dict(n=256, seed=4, fp64_n=256, prof_n=32)
 # served workload: requests with o ~ U{4..40}, v ~ U{20..300}, each the
 # sub-problem (a window of o occupied and v virtual orbitals) of one seeded
 # o=40, v=300, naux=1020 system; Poisson arrivals at 0.7x the throughput
 # measured on a closed calibration batch; mixed precision
-SERVE = dict(o_max=40, v_max=300, naux=1020, seed=5, n=48, calib=12, load=0.7, prec="bf16x3")
+SERVE = dict(o_max=40, v_max=300, naux=1020, seed=5, n=48, calib=100, load=0.7, prec="bf16x3")
 
 
 def parse():
@@ -64,8 +65,12 @@ def parse():
     ap.add_argument("--precs", default="tf32x3,bf16x3,fp64_oz",
                     help="tensor-core precisions to time (split precision and FP64 emulation)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--single-sm", action="store_true",
+                    help="split-precision contractions on single-SM tiles (M = 128) instead of SM pairs")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-tasks", type=int, default=1)
+    ap.add_argument("--err-tasks", type=int, default=16,
+                    help="tasks sampled over the task list for the per-task error of the mixed legs")
     ap.add_argument("--o", type=int, default=WORKLOAD["o"])
     ap.add_argument("--v", type=int, default=WORKLOAD["v"])
     ap.add_argument("--naux", type=int, default=WORKLOAD["naux"])
@@ -78,6 +83,11 @@ def parse():
     ap.add_argument("--no-mp2", action="store_true")
     ap.add_argument("--serve-n", type=int, default=SERVE["n"])
     ap.add_argument("--serve-prec", default=SERVE["prec"])
+    ap.add_argument("--serve-calib", type=int, default=SERVE["calib"],
+                    help="requests of the closed calibration batch that sets the arrival rate")
+    ap.add_argument("--serve-err-n", type=int, default=0,
+                    help="served results re-evaluated in FP64 emulation for their error "
+                         "(0 = every result; else a seeded sample of this many)")
     return ap.parse_args()
 
 
@@ -100,6 +110,21 @@ TF32_PER_BF16 = 1.1 / 2.25
 
 def sorted_tasks(o):
     return [(i, j, k) for i in range(o) for j in range(i, o) for k in range(j, o)]
+
+
+def sample_tasks(tasks, n, seed):
+    """n task indices (i, j, k not all equal) spread over the task list:
+    one seeded draw in each of n equal strata."""
+    from paper_1609_08094_gb300 import synth
+    u = synth.uniform(seed, 3, n)
+    out = []
+    for m in range(n):
+        lo, hi = m * len(tasks) // n, (m + 1) * len(tasks) // n
+        k = lo + int(u[m] * (hi - lo))
+        while tasks[k][0] == tasks[k][1] == tasks[k][2]:
+            k = k + 1 if k + 1 < len(tasks) else k - 1
+        out.append(k)
+    return out
 
 
 def work_tasks(tasks, first, count):
@@ -282,6 +307,15 @@ def main():
                                           f"of the o={o}, v={v} workload ({cpu_s:.1f} s)",
                "triples_per_s": len(sample) / cpu_s}
         del host, slices
+    # FP64 references of the mixed legs' errors: the first 8 tasks of their first
+    # timed batch, and each task of a seeded sample spread over the task list
+    Cm = args.mixed_tasks_per_step
+    first_m0 = partition.step_batch(ntask, rank, world, W, Cm)
+    ref8 = ref_tasks = None
+    if not args.no_mixed:
+        ref8 = t.energy_range(first_m0, min(Cm, 8))
+        samp = sample_tasks(tasks, args.err_tasks, seed + 17)
+        ref_tasks = {n: t.energy_range(n, 1)[2] for n in samp}
     t.close()
 
     # ---- mixed precision on the same sizes --------------------------------
@@ -289,7 +323,8 @@ def main():
     if not args.no_mixed:
         for prec in [x for x in args.precs.split(",") if x]:
             try:
-                tm = tcorr.Tcorr.from_instance(inst, prec=prec, profile=True, stream=stream)
+                tm = tcorr.Tcorr.from_instance(inst, prec=prec, profile=True, stream=stream,
+                                               single_sm=args.single_sm)
             except tcorr.TcorrError as e:
                 mixed[prec] = {"unavailable": str(e)}
                 continue
@@ -307,13 +342,13 @@ def main():
                    "kernel_ms_share": {k: round(m / max(1e-9, sum(mm for mm, _ in kt.values())), 4)
                                        for k, (m, _) in kt.items()},
                    "gemm_tflops": workm * fl_task / (gm * 1e-3) / 1e12 if gm > 0 else None}
-            # error vs the FP64 GPU path on the first timed batch
-            em = tm.energy_range(first_m(W), Cm)
-            tf = tcorr.Tcorr.from_instance(inst, prec="fp64", stream=stream)
-            ef = tf.energy_range(first_m(W), min(Cm, 8))
+            # error vs the FP64 GPU path: the sum of the first 8 tasks of the first
+            # timed batch, and every task of a seeded sample spread over the task list
             em8 = tm.energy_range(first_m(W), min(Cm, 8))
-            tf.close()
-            ent["rel_err_vs_fp64"] = abs(em8[2] - ef[2]) / abs(ef[2])
+            ent["rel_err_vs_fp64_first8_tasks"] = abs(em8[2] - ref8[2]) / abs(ref8[2])
+            terr = [abs(tm.energy_range(n, 1)[2] - b) / abs(b) for n, b in ref_tasks.items()]
+            ent["task_rel_err_vs_fp64"] = {"max": max(terr), "median": float(np.median(terr)),
+                                           "tasks": len(terr), "sample": "seeded, spread over the task list"}
             pk = measured_peaks()
             peak = pk["bf16"] * (TF32_PER_BF16 if prec == "tf32x3" else 1.0)
             if prec == "fp64_oz" and ent["gemm_tflops"]:
@@ -412,7 +447,45 @@ def main():
         "serving": serving,
         "rimp2": mp2,
     }
+    line["summary"] = summary(line)  # last key: a compact copy of every leg's figures
     print(json.dumps(line), flush=True)
+
+
+def summary(line):
+    """Every leg's headline figures in a few hundred characters (3 significant
+    digits): throughput, GEMM throughput, roofline fractions, errors."""
+    def r(x):
+        return None if x is None else float(f"{x:.3g}")
+
+    def get(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+
+    out = {"fp64": {"tflops": r(line["value"]), "frac": r(line["roofline"]["frac"]),
+                    "err": r(get(line, "parity", "max_rel_err_fp64"))},
+           "e2e": r(get(line, "e2e", "value"))}
+    for p, ent in (line.get("mixed") or {}).items():
+        out[p] = {"tflops": r(ent.get("value")), "gemm": r(ent.get("gemm_tflops")),
+                  "frac": r(get(ent, "roofline", "frac")), "tfrac": r(get(ent, "roofline", "tensor_frac")),
+                  "err8": r(ent.get("rel_err_vs_fp64_first8_tasks")),
+                  "err_task": r(get(ent, "task_rel_err_vs_fp64", "max"))}
+    b = {}
+    for p, ent in (get(line, "batched", "precisions") or {}).items():
+        b[p] = {"tflops": r(ent.get("value")), "x_solo": r(ent.get("speedup_vs_unbatched")),
+                "n": ent.get("molecules"), "err": r(get(ent, "rel_err_vs_fp64", "max"))}
+    out["batched"] = b
+    sv = line.get("serving") or {}
+    out["serving"] = {"n": sv.get("requests"), "p50": r(get(sv, "latency_s", "p50")),
+                      "p99": r(get(sv, "latency_s", "p99")), "tflops": r(get(sv, "throughput", "tflops")),
+                      "err": r(get(sv, "rel_err_vs_fp64", "max")), "same": sv.get("solo_vs_mixed_identical")}
+    mp = line.get("rimp2") or {}
+    out["rimp2"] = {"fp64": r(mp.get("value")), "frac": r(get(mp, "roofline", "frac"))}
+    for p, ent in (mp.get("mixed") or {}).items():
+        out["rimp2"][p] = {"tflops": r(ent.get("value")), "err": r(ent.get("rel_err_vs_fp64"))}
+    return out
 
 
 def bench_batched(args, rank, world, stream):
@@ -440,7 +513,7 @@ def bench_batched(args, rank, world, stream):
     def ntask(sub):
         return sum(i.o * (i.o + 1) * (i.o + 2) // 6 for i in sub)
 
-    def run(prec, sub, K, W):
+    def run(prec, sub, K, W, prof=True):
         with tcorr.Batch(sub, prec=prec, tune=(prec != "fp64"), stream=stream, wave_mb=args.wave_mb) as b:
             e = None
             for _ in range(W):       # the first call captures the graph
@@ -456,6 +529,8 @@ def bench_batched(args, rank, world, stream):
             ms = dist_max(ev0.elapsed_time(ev1), world) / K
             waves, launches = b.plan()
             tiles = sorted({b.tile(n)[0] for n in range(len(sub))})
+        if not prof:
+            return e, ms, waves, launches, tiles, None, None
         # kernel shares from one profiled (direct-launch) pass
         with tcorr.Batch(sub, prec=prec, tune=(prec != "fp64"), stream=stream, wave_mb=args.wave_mb,
                          profile=True) as bp:
@@ -483,40 +558,47 @@ def bench_batched(args, rank, world, stream):
                        f"seeds {BATCH['seed']}+index; {len(shapes)} on this rank",
            "generate_s": round(gen_s, 1), "precisions": {}}
     pk = measured_peaks()
+    # FP64 on every molecule (one warm-up call that captures the graph, one timed
+    # call): its energies are the reference of every mixed-precision result below;
+    # kernel shares and the unbatched comparison on the first prof_n molecules
     sub64 = insts[: max(1, args.batch_fp64_n // world)]
-    e64, ms64, wv, nl, _, kt, tot = run("fp64", sub64, K=1, W=1)
+    e64, ms64, wv, nl, _, _, _ = run("fp64", sub64, K=1, W=1, prof=False)
+    subp = insts[: max(1, BATCH["prof_n"] // world)]
+    _, msp, _, _, _, kt, tot = run("fp64", subp, K=1, W=1)
     fl64 = flops(sub64) * world
     out["precisions"]["fp64"] = {
         "molecules": len(sub64) * world, "value": fl64 / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s",
         "triples_per_s": ntask(sub64) * world / (ms64 * 1e-3), "ms_per_step": ms64, "steps": 1,
         "waves": wv, "gpu_launches": nl,
         "kernel_ms_share": {k: round(m / max(1e-9, tot), 4) for k, (m, _) in kt.items()},
-        "gemm_tflops": flops(sub64) / (kt["gemm"][0] * 1e-3) / 1e12,
-        "note": f"FP64 timed on the first {len(sub64) * world} molecules (one warm-up + one step)"}
-    ms_solo64 = solo("fp64", sub64)
+        "gemm_tflops": flops(subp) / (kt["gemm"][0] * 1e-3) / 1e12,
+        "note": f"FP64 timed on {len(sub64) * world} molecules (one warm-up + one step); kernel shares "
+                f"and the unbatched comparison on the first {len(subp) * world}"}
+    ms_solo64 = solo("fp64", subp)
     out["precisions"]["fp64"]["unbatched_ms"] = ms_solo64
-    out["precisions"]["fp64"]["speedup_vs_unbatched"] = ms_solo64 / ms64
+    out["precisions"]["fp64"]["speedup_vs_unbatched"] = ms_solo64 / msp
     for prec in [x for x in args.precs.split(",") if x]:
         try:
-            e, ms, wv, nl, tiles, kt, tot = run(prec, insts, K=args.steps, W=args.warmup)
+            e, ms, wv, nl, tiles, kt, tot = run(prec, insts, K=min(args.steps, 3), W=min(args.warmup, 3))
         except tcorr.TcorrError as err:
             out["precisions"][prec] = {"unavailable": str(err)}
             continue
         fl = flops(insts) * world
         peak = pk["bf16"] * (TF32_PER_BF16 if prec == "tf32x3" else 1.0)
         gemm_tf = flops(insts) / (kt["gemm"][0] * 1e-3) / 1e12
-        # error against the FP64 path on the molecules that were timed in FP64
+        # error of every molecule's result against its FP64 result
         rel = np.abs(e[: len(sub64), 2] - e64[:, 2]) / np.abs(e64[:, 2])
         ms_solo = solo(prec, insts)
         out["precisions"][prec] = {
             "molecules": len(insts) * world, "value": fl / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
             "triples_per_s": ntask(insts) * world / (ms * 1e-3), "ms_per_step": ms, "steps": args.steps,
-            "warmup": args.warmup, "waves": wv, "gpu_launches": nl, "tiles_pb": tiles,
+            "warmup": min(args.warmup, 3), "waves": wv, "gpu_launches": nl, "tiles_pb": tiles,
             "kernel_ms_share": {k: round(m / max(1e-9, tot), 4) for k, (m, _) in kt.items()},
             "roofline": {"bound": "tensor", "kernel": f"ugemm_tc_kernel ({prec})", "achieved": gemm_tf,
                          "peak": peak, "unit": "TFLOP/s", "frac": gemm_tf / peak, "traffic": None,
                          "tensor_achieved": 3 * gemm_tf, "tensor_frac": 3 * gemm_tf / peak},
-            "max_rel_err_vs_fp64": float(rel.max()), "tol": 1e-6,
+            "rel_err_vs_fp64": {"max": float(rel.max()), "median": float(np.median(rel)),
+                                "results": int(rel.size)}, "tol": 1e-6 if prec != "fp64_oz" else 1e-10,
             "unbatched_ms": ms_solo, "speedup_vs_unbatched": ms_solo / ms,
             "speedup_vs_fp64_batched": (fl / (ms * 1e-3)) / (fl64 / (ms64 * 1e-3))}
     return out
@@ -563,8 +645,8 @@ def bench_serving(args, rank, world, stream):
                                device=torch.device("cuda", torch.cuda.current_device()))
     torch.cuda.synchronize()
     gen_s = time.time() - t0
-    reqs = serve_requests(args.serve_n + cfg["calib"], cfg["seed"] + 100 * rank, cfg["o_max"], cfg["v_max"])
-    calib, stream_reqs = reqs[: cfg["calib"]], reqs[cfg["calib"]:]
+    reqs = serve_requests(args.serve_n + args.serve_calib, cfg["seed"] + 100 * rank, cfg["o_max"], cfg["v_max"])
+    calib, stream_reqs = reqs[: args.serve_calib], reqs[args.serve_calib:]
     prec = args.serve_prec
     # mean work per request of the size distribution (large sample of the same law)
     dist = serve_requests(20000, cfg["seed"] + 7, cfg["o_max"], cfg["v_max"])
@@ -612,6 +694,22 @@ def bench_serving(args, rank, world, stream):
             jid = solo.submit(window(base, *stream_reqs[k]))
             solo.drain()
             same += int(solo.poll(jid)[1] == res[k][1])
+    # the error of every served result against the FP64-accurate path (FP64
+    # emulation on the tensor cores, held to 1e-10 of the oracle by the tests),
+    # all requests through one FP64-emulation server after the timed stream
+    t_ref = time.perf_counter()
+    if args.serve_err_n > 0 and args.serve_err_n < len(stream_reqs):
+        pick = sorted(set(int(x) for x in synth.uniform(cfg["seed"] + 9, 31, args.serve_err_n)
+                          * len(stream_reqs)))
+    else:
+        pick = list(range(len(stream_reqs)))
+    with tcorr.Server(prec="fp64_oz", stream=stream) as ref_srv:
+        rid = {k: ref_srv.submit(window(base, *stream_reqs[k])) for k in pick}
+        ref_srv.drain()
+        ref_e = {k: ref_srv.poll(j) for k, j in rid.items()}
+    ref_s = time.perf_counter() - t_ref
+    errs = np.array([abs(res[k][1][2] - ref_e[k][1][2]) / abs(ref_e[k][1][2])
+                     for k in pick if res[k][0] == "done" and ref_e[k][0] == "done"])
     fl = sum(req_flops(o, v) for o, v, _, _ in stream_reqs)
     makespan = dist_max(makespan, world)
     return {"workload": f"{len(stream_reqs)} requests per GPU, o ~ U{{4..{cfg['o_max']}}}, "
@@ -625,7 +723,12 @@ def bench_serving(args, rank, world, stream):
             "throughput": {"requests_per_s": len(stream_reqs) * world / makespan,
                            "tflops": fl * world / makespan / 1e12, "makespan_s": makespan},
             "waves": st1["waves"] - st0["waves"], "peak_admitted_bytes": st1["peak_bytes"],
-            "solo_vs_mixed_identical": f"{same}/{len(sample)}", "generate_s": round(gen_s, 1)}
+            "solo_vs_mixed_identical": f"{same}/{len(sample)}", "generate_s": round(gen_s, 1),
+            "rel_err_vs_fp64": {"max": float(errs.max()) if errs.size else None,
+                                "median": float(np.median(errs)) if errs.size else None,
+                                "results": int(errs.size), "tol": 1e-6,
+                                "reference": (f"{'every served request' if len(pick) == len(stream_reqs) else f'a seeded sample of {len(pick)} served requests'}"
+                                              f" again in FP64 emulation ({ref_s:.0f} s)")}}
 
 
 def bench_mp2(args, rank, world, stream):

@@ -49,15 +49,29 @@ typedef enum {
 typedef enum {
     TCORR_FP64 = 0,    /* W contractions and energy in FP64 (FP64 pipe) */
     TCORR_TF32X3 = 1,  /* W contractions on tcgen05 tensor cores, TF32 hi+lo split, 3 products,
-                          FP32 accumulation; denominators and energy sum in FP64 (Sec. 3 mixed
-                          precision, re-designed) */
-    TCORR_BF16X3 = 2,  /* as TF32X3 with BF16 hi+lo operands */
+                          FP32 accumulation, W stored in FP32 (Sec. 3 mixed precision,
+                          re-designed).  Energy epilogue: the numerators sum Z W and sum Z Y of
+                          each element orbit in FP32; the denominator e_i+e_j+e_k-e_a-e_b-e_c
+                          in FP64 and its reciprocal to FP64 accuracy (an FP32 reciprocal
+                          refined by one Newton step in FP64); numerator x 1/D and every sum
+                          (per thread, warp, CTA, orbit, task, problem) in FP64 */
+    TCORR_BF16X3 = 2,  /* as TF32X3 with BF16 hi+lo operands.  A BF16 hi+lo split keeps 16
+                          significant bits, and its residual averages below the 1e-6 bound only
+                          over enough work: problems below 1e11 algorithmic flops (12 v^3 (v+o)
+                          per task with i, j, k not all equal) run on TF32 hi+lo operands
+                          instead (same products and kernels, so their results are identical
+                          to TCORR_TF32X3's) -- in single, batch and server handles alike */
     TCORR_FP64_OZ = 3  /* FP64-accurate W contractions on the BF16 tensor cores: each operand split
                           into 5 signed 7-bit slices under one power-of-two scale per operand side
                           (Ozaki scheme), slice products summed exactly in FP32 per 32-element K
                           chunk and in int64 across chunks, U rounded once to FP64; FP64 energy
                           epilogue.  sm_103 only; device or host inputs; batch and server too */
 } tcorr_precision;
+
+/* TCORR_BF16X3 problems below this many algorithmic flops run on TF32 operands */
+#define TCORR_BF16_MIN_FLOPS 1e11
+/* TCORR_BF16X3 RI-MP2 problems below this many (pair, a, b, gamma) terms run on TF32 operands */
+#define TCORR_MP2_BF16_MIN_TERMS 16777216.0
 
 typedef struct {
     int prec;           /* tcorr_precision; 0 = TCORR_FP64 */
@@ -77,6 +91,9 @@ typedef struct {
     int wave_mb;        /* batch handle: U scratch per wave in MiB (0 = 96, sized so that one
                            wave's U stays in L2 between the contraction and the epilogue);
                            raised to one task of the largest problem when smaller */
+    int single_sm;      /* split precisions: 0 = W contractions on SM pairs (2-CTA clusters,
+                           tcgen05 cta_group::2, M = 256 tiles: each SM loads its own A tile and
+                           half of B); 1 = one SM per tile (M = 128) */
 } tcorr_opts;           /* zero-initialised = defaults */
 
 /*
@@ -305,7 +322,10 @@ tcorr_status tcorr_server_destroy(tcorr_server_t s);
  * with the assembly on the sm_103 tensor cores in TF32 or BF16 hi + lo split
  * precision (all four products: the lo*lo term is kept, as the same-index
  * elements of i = j pairs are sums of squares; FP32 accumulation, FP32 energy
- * terms, FP64 sums).
+ * terms, FP64 sums).  TCORR_BF16X3 problems with fewer than 2^24
+ * (pair i <= j, a, b, gamma) terms run on TF32 hi + lo operands instead (the
+ * BF16 split's residual averages below 1e-6 only over more terms); their
+ * results are identical to TCORR_TF32X3's.
  *
  *   eps_occ [o], eps_vir [v], C [naux][v][o] = C^gamma_ai (row-major float64;
  *   device pointers, or host pointers with opts.host_inputs = 1; read only

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ugemm_oz_kernel(const __grid_co
                         }
                         tc_fence_after();
                         const uint32_t sA = sbase + stage * OZ_STAGE, sB = sA + OZ_S * OZ_A;
-                        const int nks = chunk_ksteps<2>(kv, ko, dp, lp, ch);
+                        const int nks = chunk_ksteps(2, kv, ko, dp, lp, ch);
                         // descriptors are linear in the address (its low field is addr >> 4), so every
                         // plane / K-step descriptor is the stage's base descriptor plus a constant
                         const uint64_t dA = sdesc(sA), dB = sdesc(sB);

@@ -64,7 +64,8 @@ constexpr int B_BYTES = BN * ROW_BYTES; // 16 KB
 // largest B tile (brows rows): 4 stages for 256-row B tiles, up to 8 for small v
 constexpr int RING_BYTES = 4 * (2 * A_BYTES + 2 * B_BYTES);
 constexpr int SMEM_BYTES = RING_BYTES + 1024;
-template <int KIND>
+// The operand type (TF32 or BF16) is a property of each problem (InstDesc::kind),
+// so problems of both types can share a wave.
 __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_constant__ Wave wv) {
     extern __shared__ __align__(1024) uint8_t smem_dyn[];
     __shared__ __align__(8) uint64_t bar_full[MAX_STAGES], bar_empty[MAX_STAGES];
@@ -103,10 +104,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
     tc_fence_after();
     const uint32_t tmem = tmem_holder;
 
-    const int kch = ROW_BYTES / (KIND == 1 ? 4 : 2);
     // instruction descriptor: D = F32, A/B = TF32 (2) or BF16 (1), K-major, M = 128
-    constexpr uint32_t fmt = KIND == 1 ? 2u : 1u;
-    constexpr uint32_t idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BM >> 4) << 24);
+    constexpr uint32_t idesc_m = (1u << 4) | ((uint32_t)(BM >> 4) << 24);
 
     if (warp == 0) {
         if (lane == 0) {
@@ -123,6 +122,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                 if (w.diag) continue;
                 const InstDesc &d = *sc.d;
                 const int o = d.dm.o, kv = d.kv, ko = d.ko, nch = num_chunks(d);
+                const int kch = ROW_BYTES / (d.kind == 1 ? 4 : 2);
                 const int s = w.s, pp = w.p, q = w.q;
                 const int cb = w.bt * d.pb, cc = w.ct * d.pc, ca = w.n * d.brows;
                 const uint32_t stage_tx = d.stage_tx;
@@ -186,10 +186,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                 const InstDesc &d = *sc.d;
                 // per-item constants in registers: the issue loop reads no memory
                 const int kv = d.kv, ko = d.ko, dp = d.dm.dp, lp = d.dm.lp;
-                const int nch = 2 * kv + 2 * ko, kb = d.kb;
+                const int nch = 2 * kv + 2 * ko, kb = d.kb, kind = d.kind;
                 const int nvalid = min(d.brows, d.dm.v - w.n * d.brows);
                 const int N = (nvalid + 15) / 16 * 16;
-                const uint32_t idesc = idesc_base | ((uint32_t)(N >> 3) << 17);
+                const uint32_t fmt = kind == 1 ? 2u : 1u;
+                const uint32_t idesc = idesc_m | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17);
                 // K blocks of kb chunks: the small hi*lo and lo*hi products of each
                 // chunk are issued as its data lands, the dominant hi*hi products of
                 // the whole block last, so that the truncation of every instruction
@@ -213,15 +214,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                         }
                         tc_fence_after();
                         const uint32_t dt = tmem + buf * (uint32_t)BN;
-                        const uint32_t sA = sbase + stage * stage_bytes, sAl = sA + A_BYTES;
-                        const uint32_t sB = sAl + A_BYTES, sBl = sB + b_plane;
-                        const int nks = chunk_ksteps<KIND>(kv, ko, dp, lp, c0 + cb);
-                        for (int kk = 0; kk < nks; kk++) {
-                            const uint32_t off = kk * 32;
-                            tc_mma<KIND>(dt, sdesc(sA + off), sdesc(sBl + off), idesc,
-                                         (cb > 0 || kk > 0) ? 1u : 0u);
-                            tc_mma<KIND>(dt, sdesc(sAl + off), sdesc(sB + off), idesc, 1u);
-                        }
+                        const uint32_t sA = sbase + stage * stage_bytes;
+                        const int nks = chunk_ksteps(kind, kv, ko, dp, lp, c0 + cb);
+                        if (kind == 1) issue_lo_products<1, 1>(dt, sA, A_BYTES, b_plane, nks, idesc, cb == 0);
+                        else issue_lo_products<2, 1>(dt, sA, A_BYTES, b_plane, nks, idesc, cb == 0);
                         if (++stage == nst) { stage = 0; phase ^= 1u; }
                     }
                     if (!ok) break;
@@ -230,12 +226,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                     // so far has completed) right after its last product is issued
                     int sj = st0;
                     for (int cb = 0; cb < nb; cb++) {
-                        const uint32_t sA = sbase + sj * stage_bytes, sB = sA + 2 * A_BYTES;
-                        const int nks = chunk_ksteps<KIND>(kv, ko, dp, lp, c0 + cb);
-                        for (int kk = 0; kk < nks; kk++) {
-                            const uint32_t off = kk * 32;
-                            tc_mma<KIND>(dt, sdesc(sA + off), sdesc(sB + off), idesc, 1u);
-                        }
+                        const uint32_t sA = sbase + sj * stage_bytes;
+                        const int nks = chunk_ksteps(kind, kv, ko, dp, lp, c0 + cb);
+                        if (kind == 1) issue_hi_products<1, 1>(dt, sA, A_BYTES, nks, idesc);
+                        else issue_hi_products<2, 1>(dt, sA, A_BYTES, nks, idesc);
                         tc_commit(smem_u32(&bar_empty[sj]));
                         if (++sj == nst) sj = 0;
                     }
@@ -344,13 +338,372 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
     }
 }
 
+// ---- SM-pair variant (tcgen05 cta_group::2) ---------------------------------
+//
+// Two CTAs of a thread-block cluster (one per SM of an SM pair) compute one
+// M = 256 tile: each loads its own 128-pair A tile and half of the B tile
+// (N/2 rows of a), and one thread of the even CTA ("leader") issues
+// tcgen05.mma.cta_group::2, which reads A and B from both CTAs' shared memory
+// and accumulates each CTA's 128 rows in that CTA's tensor memory.  Per K
+// chunk an SM then ingests 16 KB of A and N/2 x 128 bytes of B (32 KB at
+// N = 256) instead of 48 KB, for the same tensor work per SM: the per-SM
+// operand-ingest rate, not the tensor pipe, bounds the single-SM kernel.
+//
+// The pair's two 128-pair tiles are consecutive tiles of the flattened
+// (b tile, c tile) list of a group: work item = (task, group, tile pair,
+// N pass); a tile index past the list is TMA zero fill and is not stored.
+//
+// Hand-offs (all bounded waits, as in the single-SM kernel):
+//  - each CTA's producer waits on its own "empty" barrier of a stage (the
+//    leader's MMA commits arrive on both CTAs' barriers), and signals its
+//    loads on the LEADER's "full" barrier, for which the leader's producer
+//    expects the bytes of both CTAs;
+//  - the leader's MMA commits each accumulator block to both CTAs' "hfull"
+//    barriers; each drain warp of either CTA arrives once on the leader's
+//    "hempty" barrier (16 arrivals) when it has read the block;
+//  - an expired wait sets the abort flag of both CTAs and the device error
+//    flag; before the pair tears down, the leader waits (bounded) for its
+//    issued MMAs, and a producer that aborted lets its copies in flight land.
+// Teardown: a cluster barrier (every role of both CTAs ends after bounded
+// waits), then both CTAs free the pair's tensor memory.
+constexpr int PAIR_HEMPTY_ARRIVALS = 2 * (EPI_THREADS / 32);
+
+struct PairItem {
+    Item it;
+    bool empty;  // this CTA's tile index lies past the group's tile list
+};
+__device__ __forceinline__ PairItem decode_pair(const Wave &w, int64_t it, SegCache &c, uint32_t rank) {
+    seg_update(w, it, c);
+    PairItem r;
+    const int npt = c.nbt * c.nct;
+    const int npair = (npt + 1) / 2;
+    int64_t x = it - c.begin;
+    r.it.n = (int)(x % c.npass);
+    x /= c.npass;
+    const int t = (int)(x % npair) * 2 + (int)rank;
+    x /= npair;
+    r.it.g = (int)(x % 3);
+    r.it.tb = (int)(x / 3);
+    r.empty = t >= npt;
+    r.it.bt = r.empty ? c.nbt : t / c.nct;  // past the list: b >= v, all TMA fill
+    r.it.ct = r.empty ? 0 : t % c.nct;
+    if (r.it.tb != c.tcached) {
+        const int *tk = c.d->tasks + 3 * (c.task0 + r.it.tb);
+        c.ti = tk[0];
+        c.tj = tk[1];
+        c.tk = tk[2];
+        c.tcached = r.it.tb;
+    }
+    const int i = c.ti, j = c.tj, k = c.tk;
+    r.it.diag = (i == j && j == k);
+    if (r.it.g == 0) { r.it.s = i; r.it.p = j; r.it.q = k; }
+    else if (r.it.g == 1) { r.it.s = j; r.it.p = i; r.it.q = k; }
+    else { r.it.s = k; r.it.p = i; r.it.q = j; }
+    return r;
+}
+// abort both CTAs of the pair and raise the device error flag
+__device__ __forceinline__ void fail_pair(volatile int *abort_flag, uint32_t peer_abort_cl, int *err, int code) {
+    *abort_flag = 1;
+    st_cluster_u32(peer_abort_cl, 1u);
+    atomicOr(err, code);
+}
+__device__ __forceinline__ void spin_ns(uint64_t ns) {
+    const uint64_t t0 = gtimer();
+    while (gtimer() - t0 < ns) {
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_pair_kernel(const __grid_constant__ Wave wv) {
+    extern __shared__ __align__(1024) uint8_t smem_dyn[];
+    __shared__ __align__(8) uint64_t bar_full[MAX_STAGES], bar_empty[MAX_STAGES];
+    __shared__ __align__(8) uint64_t bar_hfull[2], bar_hempty[2];
+    __shared__ __align__(8) uint64_t bar_fin;
+    __shared__ uint32_t tmem_holder;
+    __shared__ volatile int abort_sh;
+    __shared__ SegCache ecache[EPI_THREADS / 32];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank(), cid = cluster_id(), ncl = cluster_count();
+    const bool leader = rank == 0;
+    const uint32_t sbase = (smem_u32(smem_dyn) + 1023u) & ~1023u;
+    const uint32_t b_half = (uint32_t)wv.tc_brows / 2;                       // B rows per CTA
+    const uint32_t b_plane = (b_half * ROW_BYTES + 1023u) & ~1023u;
+    const uint32_t stage_bytes = 2u * A_BYTES + 2u * b_plane;
+    const int nst = min(MAX_STAGES, (int)(RING_BYTES / stage_bytes));
+    const uint32_t peer_abort = peer_addr(smem_u32((const void *)&abort_sh), rank ^ 1u);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < nst; s++) {
+            mbar_init(smem_u32(&bar_full[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(smem_u32(&bar_hfull[b]), 1);
+            mbar_init(smem_u32(&bar_hempty[b]), PAIR_HEMPTY_ARRIVALS);
+        }
+        mbar_init(smem_u32(&bar_fin), 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_holder)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();  // both CTAs' barriers exist before any remote signal
+    tc_fence_after();
+    const uint32_t tmem = tmem_holder;
+    // instruction descriptor: D = F32, K-major A and B, M = 256 over the pair
+    constexpr uint32_t idesc_m = (1u << 4) | ((uint32_t)(2 * BM >> 4) << 24);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int last_phase[MAX_STAGES];
+            for (int s = 0; s < MAX_STAGES; s++) last_phase[s] = -1;
+            bool ok = true;
+            bool inject = wv.inject_stall != 0 && cid == 0 && leader;
+            SegCache sc;
+            seg_reset(sc);
+            for (int64_t it = cid; it < wv.n_gemm && ok; it += ncl) {
+                const PairItem pw = decode_pair(wv, it, sc, rank);
+                const Item &w = pw.it;
+                if (w.diag) continue;
+                const InstDesc &d = *sc.d;
+                const int o = d.dm.o, kv = d.kv, ko = d.ko, nch = num_chunks(d);
+                const int kch = ROW_BYTES / (d.kind == 1 ? 4 : 2);
+                const int s = w.s, pp = w.p, q = w.q;
+                const int nvalid = min(d.brows, d.dm.v - w.n * d.brows);
+                const int N = (nvalid + 15) / 16 * 16;
+                const int cb = w.bt * d.pb, cc = w.ct * d.pc, ca = w.n * d.brows + (int)rank * (N / 2);
+                const uint32_t stage_tx = d.stage_tx;  // both CTAs' bytes
+                for (int ch = 0; ch < nch; ch++) {
+                    if (!mbar_wait_cl(smem_u32(&bar_empty[stage]), phase ^ 1u, &abort_sh)) {
+                        fail_pair(&abort_sh, peer_abort, wv.err, DERR_TIMEOUT_EMPTY);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t full = smem_u32(&bar_full[stage]);
+                    if (leader) mbar_expect_tx(full, stage_tx);
+                    const uint32_t full_l = peer_addr(full, 0);
+                    last_phase[stage] = (int)phase;
+                    const uint32_t sA = sbase + stage * stage_bytes, sAl = sA + A_BYTES;
+                    const uint32_t sB = sAl + A_BYTES, sBl = sB + b_plane;
+                    int seg, kk;
+                    if (ch < kv) { seg = 0; kk = ch; }
+                    else if (ch < 2 * kv) { seg = 1; kk = ch - kv; }
+                    else if (ch < 2 * kv + ko) { seg = 2; kk = ch - 2 * kv; }
+                    else { seg = 3; kk = ch - 2 * kv - ko; }
+                    const int k0 = kk * kch;
+                    int amap, aslice, bmap, brow;
+                    switch (seg) {
+                        case 0: amap = MAP_G_NAT; aslice = q; bmap = MAP_T2R; brow = s * o + pp; break;
+                        case 1: amap = MAP_G_SWP; aslice = pp; bmap = MAP_T2R; brow = s * o + q; break;
+                        case 2: amap = MAP_T2K_NAT; aslice = pp; bmap = MAP_AON; brow = q * o + s; break;
+                        default: amap = MAP_T2K_SWP; aslice = q; bmap = MAP_AON; brow = pp * o + s; break;
+                    }
+                    if (inject) {
+                        inject = false;
+                        last_phase[stage] = -1;  // the leader's bytes never come: the MMA's wait must expire
+                    } else {
+                        tma_load_4d_pair(sA, &d.maps[amap][0], full_l, k0, cc, cb, aslice);
+                        tma_load_4d_pair(sAl, &d.maps[amap][1], full_l, k0, cc, cb, aslice);
+                        tma_load_3d_pair(sB, &d.maps[bmap][0], full_l, k0, ca, brow);
+                        tma_load_3d_pair(sBl, &d.maps[bmap][1], full_l, k0, ca, brow);
+                    }
+                    if (++stage == nst) { stage = 0; phase ^= 1u; }
+                }
+            }
+            if (!ok) {
+                // let the copies in flight land: the leader sees both CTAs' bytes on
+                // its own full barriers; the peer gives its own copies a fixed time
+                if (leader) {
+                    for (int s = 0; s < nst; s++) {
+                        if (last_phase[s] < 0) continue;
+                        const uint64_t t0 = gtimer();
+                        while (!mbar_test_cl(smem_u32(&bar_full[s]), (uint32_t)last_phase[s]) &&
+                               gtimer() - t0 < WAIT_LIMIT_NS) {
+                        }
+                    }
+                }
+                spin_ns(1000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t hblk = 0;
+            bool ok = true;
+            SegCache sc;
+            seg_reset(sc);
+            for (int64_t it = cid; it < wv.n_gemm && ok; it += ncl) {
+                const PairItem pw = decode_pair(wv, it, sc, rank);
+                const Item &w = pw.it;
+                if (w.diag) continue;
+                const InstDesc &d = *sc.d;
+                const int kv = d.kv, ko = d.ko, dp = d.dm.dp, lp = d.dm.lp;
+                const int nch = 2 * kv + 2 * ko, kb = d.kb, kind = d.kind;
+                const int nvalid = min(d.brows, d.dm.v - w.n * d.brows);
+                const int N = (nvalid + 15) / 16 * 16;
+                const uint32_t fmt = kind == 1 ? 2u : 1u;
+                const uint32_t idesc = idesc_m | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17);
+                // the same K-block order as the single-SM kernel: small products
+                // of each chunk as it lands, the block's hi*hi products last
+                for (int c0 = 0; c0 < nch && ok; c0 += kb) {
+                    const int nb = min(kb, nch - c0);
+                    const uint32_t buf = hblk & 1u;
+                    int st0 = stage;
+                    for (int cb = 0; cb < nb; cb++) {
+                        if (!mbar_wait_cl(smem_u32(&bar_full[stage]), phase, &abort_sh)) {
+                            fail_pair(&abort_sh, peer_abort, wv.err, DERR_TIMEOUT_FULL);
+                            ok = false;
+                            break;
+                        }
+                        if (cb == 0 &&
+                            !mbar_wait_cl(smem_u32(&bar_hempty[buf]), ((hblk >> 1) & 1u) ^ 1u, &abort_sh)) {
+                            fail_pair(&abort_sh, peer_abort, wv.err, DERR_TIMEOUT_TMEM);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t dt = tmem + buf * (uint32_t)BN;
+                        const uint32_t sA = sbase + stage * stage_bytes;
+                        const int nks = chunk_ksteps(kind, kv, ko, dp, lp, c0 + cb);
+                        if (kind == 1) issue_lo_products<1, 2>(dt, sA, A_BYTES, b_plane, nks, idesc, cb == 0);
+                        else issue_lo_products<2, 2>(dt, sA, A_BYTES, b_plane, nks, idesc, cb == 0);
+                        if (++stage == nst) { stage = 0; phase ^= 1u; }
+                    }
+                    if (!ok) break;
+                    const uint32_t dt = tmem + buf * (uint32_t)BN;
+                    int sj = st0;
+                    for (int cb = 0; cb < nb; cb++) {
+                        const uint32_t sA = sbase + sj * stage_bytes;
+                        const int nks = chunk_ksteps(kind, kv, ko, dp, lp, c0 + cb);
+                        if (kind == 1) issue_hi_products<1, 2>(dt, sA, A_BYTES, nks, idesc);
+                        else issue_hi_products<2, 2>(dt, sA, A_BYTES, nks, idesc);
+                        tc_commit_pair(smem_u32(&bar_empty[sj]), (uint16_t)3);
+                        if (++sj == nst) sj = 0;
+                    }
+                    tc_commit_pair(smem_u32(&bar_hfull[buf]), (uint16_t)3);
+                    hblk++;
+                }
+            }
+            // every MMA issued by this thread has completed before the pair tears down
+            tc_commit_pair(smem_u32(&bar_fin), (uint16_t)1);
+            const uint64_t t0 = gtimer();
+            while (!mbar_test_cl(smem_u32(&bar_fin), 0u) && gtimer() - t0 < WAIT_LIMIT_NS) {
+            }
+        }
+    } else {
+        const int wq = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int row = wq * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+        uint32_t hblk = 0;
+        bool ok = true;
+        SegCache &cs = ecache[warp - 2];
+        if (lane == 0) seg_reset(cs);
+        __syncwarp();
+        for (int64_t it = cid; it < wv.n_gemm && ok; it += ncl) {
+            SegCache sc = cs;
+            const PairItem pw = decode_pair(wv, it, sc, rank);
+            const Item &w = pw.it;
+            __syncwarp();
+            if (lane == 0) cs = sc;
+            __syncwarp();
+            if (w.diag) continue;
+            const InstDesc &d = *sc.d;
+            const int64_t u_seg = sc.u_off;
+            const int v = d.dm.v, vc = d.dm.vc;
+            const int nhb = (num_chunks(d) + d.kb - 1) / d.kb;
+            const int lb = row / d.pc, lc = row % d.pc;
+            const int pass0 = w.n * d.brows, pass_end = min(v, pass0 + d.brows);
+            const int N = (pass_end - pass0 + 15) / 16 * 16;
+            const int wh = N > 128 ? 128 : (N > 64 ? 64 : 32);
+            const int nld = wh / 32;
+            float total[128];
+#pragma unroll
+            for (int j = 0; j < 128; j++) total[j] = 0.f;
+            for (int hb = 0; hb < nhb; hb++) {
+                const uint32_t buf = hblk & 1u;
+                int good = 1;
+                if (lane == 0) good = mbar_wait_cl(smem_u32(&bar_hfull[buf]), (hblk >> 1) & 1u, &abort_sh) ? 1 : 0;
+                good = __shfl_sync(0xffffffffu, good, 0);
+                __syncwarp();
+                if (!good) { ok = false; break; }
+                tc_fence_after();
+#pragma unroll
+                for (int c4 = 0; c4 < 4; c4++) {
+                    if (c4 < nld) {
+                        uint32_t r[16], r2[16];
+                        const uint32_t ta = tmem + lane_off + buf * (uint32_t)BN + (uint32_t)(half * wh + c4 * 32);
+                        tc_ld16(ta, r);
+                        tc_ld16(ta + 16, r2);
+                        tc_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 16; j++) total[c4 * 32 + j] += __uint_as_float(r[j]);
+#pragma unroll
+                        for (int j = 0; j < 16; j++) total[c4 * 32 + 16 + j] += __uint_as_float(r2[j]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(peer_addr(smem_u32(&bar_hempty[buf]), 0));
+                hblk++;
+            }
+            if (!ok) {
+                if (lane == 0) fail_pair(&abort_sh, peer_abort, wv.err, DERR_TIMEOUT_TMEM);
+                break;
+            }
+            if (pw.empty) continue;
+            const int b = w.bt * d.pb + lb, c = w.ct * d.pc + lc;
+            if (b < v && c < v) {
+                const int a0 = pass0 + half * wh;
+                const int64_t stride = w.g == 1 ? (int64_t)vc : (int64_t)v * vc;
+                const int64_t base = w.g == 1 ? (int64_t)b * v * vc + c : (int64_t)b * vc + c;
+                const int64_t u_off = u_seg + (int64_t)(w.tb * 3 + w.g) * v * v * vc;
+                float *Ug = static_cast<float *>(wv.U) + u_off + base + (int64_t)a0 * stride;
+                const int na = min(wh, pass_end - a0);
+                if (na == 128) {
+#pragma unroll
+                    for (int j = 0; j < 128; j++) {
+                        *Ug = total[j];
+                        Ug += stride;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 128; j++) {
+                        if (j < na) *Ug = total[j];
+                        Ug += stride;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();  // the peer no longer signals this CTA's barriers or reads its operands
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                     : "memory");
+    }
+}
+
 }  // namespace
 
 using tcx::encode;
 
 bool tc_supported(int cc_major, int cc_minor) { return cc_major == 10 && cc_minor == 3; }
 
-cudaError_t tc_fill_desc(InstDesc &d, int prec, const Operands &op, int pb, int kb, std::string &err) {
+cudaError_t tc_fill_desc(InstDesc &d, int prec, const Operands &op, int pb, int kb, bool pair, std::string &err) {
     if (pb != 4 && pb != 8 && pb != 16) {
         err = "tensor-core pair tile: pb must be 4, 8 or 16";
         return cudaErrorInvalidValue;
@@ -368,15 +721,23 @@ cudaError_t tc_fill_desc(InstDesc &d, int prec, const Operands &op, int pb, int 
     d.pb = pb;
     d.pc = pc;
     d.kb = kb;
+    d.kind = tf ? 1 : 2;
+    d.pair = pair ? 1 : 0;
     d.nbt = (v + pb - 1) / pb;
     d.nct = (v + pc - 1) / pc;
     d.npass = (v + BN - 1) / BN;
-    d.brows = round_up((v + d.npass - 1) / d.npass, 16);  // pass width: <= BN
+    // pass width: <= BN, a multiple of 16 (single SM) or of 32 (SM pair: the pair
+    // MMA's N is a multiple of 32, each SM holding N / 2 rows of B)
+    const int wq = pair ? 32 : 16;
+    d.brows = round_up((v + d.npass - 1) / d.npass, wq);
     d.kv = (v + kch - 1) / kch;
     d.ko = (o + kch - 1) / kch;
-    d.stage_tx = (uint32_t)(2 * A_BYTES + 2 * d.brows * ROW_BYTES);
+    // bytes per stage: one CTA's (single SM), or both CTAs' (the pair's leader expects them all)
+    d.stage_tx = pair ? (uint32_t)(2 * (2 * A_BYTES + 2 * (d.brows / 2) * ROW_BYTES))
+                      : (uint32_t)(2 * A_BYTES + 2 * d.brows * ROW_BYTES);
     const uint64_t V = v, O = o;
-    const uint32_t bk = (uint32_t)kch, bpc = (uint32_t)pc, bpb = (uint32_t)pb, brows = (uint32_t)d.brows;
+    const uint32_t bk = (uint32_t)kch, bpc = (uint32_t)pc, bpb = (uint32_t)pb;
+    const uint32_t brows = (uint32_t)(pair ? d.brows / 2 : d.brows);  // B box rows per CTA
     void *hi[4] = {op.G, op.T2K, op.T2R, op.AoN};
     void *lo[4] = {op.Glo, op.T2Klo, op.T2Rlo, op.AoNlo};
     for (int part = 0; part < 2; part++) {
@@ -423,30 +784,77 @@ cudaError_t tc_fill_desc(InstDesc &d, int prec, const Operands &op, int pb, int 
     return cudaSuccess;
 }
 
-int64_t tc_units_per_task(const InstDesc &d) { return (int64_t)3 * d.nbt * d.nct * d.npass; }
+int64_t tc_units_per_task(const InstDesc &d) {
+    const int64_t tiles = (int64_t)d.nbt * d.nct;
+    return (int64_t)3 * (d.pair ? (tiles + 1) / 2 : tiles) * d.npass;
+}
 
-cudaError_t tc_prepare(int prec) {
+cudaError_t tc_prepare(int) {
     static std::mutex mu;
-    static bool done[2] = {false, false};
+    static bool done = false;
     std::lock_guard<std::mutex> lk(mu);
-    const int t = prec == TCORR_TF32X3 ? 0 : 1;
-    if (done[t]) return cudaSuccess;
-    const cudaError_t e = t == 0 ? cudaFuncSetAttribute(ugemm_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                        SMEM_BYTES)
-                                 : cudaFuncSetAttribute(ugemm_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                        SMEM_BYTES);
-    if (e == cudaSuccess) done[t] = true;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(ugemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ugemm_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess) done = true;
     return e;
 }
 
-cudaError_t launch_ugemm_tc(int prec, int sm_count, const Wave &w, cudaStream_t st) {
-    const int grid = (int)std::min<int64_t>(sm_count, w.n_gemm);
-    if (grid <= 0) return cudaSuccess;
-    if (w.tc_brows < 16 || w.tc_brows > BN || w.tc_brows % 16 != 0) return cudaErrorInvalidValue;
-    const cudaError_t e = tc_prepare(prec);
+// Co-resident 2-CTA clusters of the pair kernel on the current device (one
+// per SM pair that the cluster scheduler can place), queried once per device.
+static int pair_clusters(int sm_count) {
+    static std::mutex mu;
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return sm_count / 2;
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache[dev] > 0) return cache[dev];
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(sm_count / 2 * 2), 1, 1);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, ugemm_tc_pair_kernel, &cfg) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = sm_count / 2;
+    }
+    cache[dev] = std::min(n, sm_count / 2);
+    return cache[dev];
+}
+
+cudaError_t launch_ugemm_tc(int prec, int sm_count, const Wave &w, cudaStream_t st, bool pair) {
+    if (w.n_gemm <= 0) return cudaSuccess;
+    if (w.tc_brows < 16 || w.tc_brows > BN || w.tc_brows % (pair ? 32 : 16) != 0) return cudaErrorInvalidValue;
+    cudaError_t e = tc_prepare(prec);
     if (e != cudaSuccess) return e;
-    if (prec == TCORR_TF32X3) ugemm_tc_kernel<1><<<grid, TC_THREADS, SMEM_BYTES, st>>>(w);
-    else ugemm_tc_kernel<2><<<grid, TC_THREADS, SMEM_BYTES, st>>>(w);
+    if (!pair) {
+        const int grid = (int)std::min<int64_t>(sm_count, w.n_gemm);
+        ugemm_tc_kernel<<<grid, TC_THREADS, SMEM_BYTES, st>>>(w);
+        return cudaGetLastError();
+    }
+    const int ncl = (int)std::min<int64_t>(pair_clusters(sm_count), w.n_gemm);
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(2 * ncl), 1, 1);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, ugemm_tc_pair_kernel, w);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

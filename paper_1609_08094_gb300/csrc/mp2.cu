@@ -273,6 +273,13 @@ tcorr_status tcorr_mp2_create(tcorr_mp2_t *out, int o, int v, int naux, const do
         return TCORR_ENOMEM;
     }
     Exec &ex = h->ex;
+    // BF16 hi + lo operands on small problems: the split's residual (up to 2^-17
+    // of each operand) averages below the 1e-6 bound only over enough terms.  Over
+    // seeded shapes the BF16X3 error reached 1.3e-6 at 1.2e3 (pair, a, b, gamma)
+    // terms and 3.5e-7 at 4e6, and stayed below 3.1e-7 above 1e7, while TF32X3
+    // stayed within 2.9e-7 throughout: problems below 2^24 terms run on TF32
+    // hi + lo operands (same four products, same kernel).
+    if (op.prec == TCORR_BF16X3 && (double)o * (o + 1) / 2 * v * v * naux < TCORR_MP2_BF16_MIN_TERMS) op.prec = TCORR_TF32X3;
     try {
         init_exec(ex, op, stream);  // SM count; split precision only on the sm_103 tensor cores
         const bool split = op.prec != TCORR_FP64;

@@ -86,6 +86,16 @@ void resolve_timers(Exec &ex) {
     ex.pending.swap(keep);
 }
 
+double problem_flops(int o, int v) {
+    const double tasks = (double)o * (o + 1) * (o + 2) / 6.0 - o;  // i = j = k tasks carry no work
+    return tasks * 12.0 * (double)v * v * v * (double)(v + o);
+}
+
+int operand_prec(int prec, int o, int v) {
+    if (prec == TCORR_BF16X3 && problem_flops(o, v) < BF16_MIN_FLOPS) return TCORR_TF32X3;
+    return prec;
+}
+
 int elem_kind(int prec) { return prec == TCORR_FP64 ? 0 : (prec == TCORR_TF32X3 ? 1 : (prec == TCORR_BF16X3 ? 2 : 3)); }
 bool is_split(int prec) { return prec == TCORR_TF32X3 || prec == TCORR_BF16X3; }
 bool fp64_epilogue(int prec) { return prec == TCORR_FP64 || prec == TCORR_FP64_OZ; }
@@ -172,8 +182,9 @@ void build_operands(Exec &ex, Problem &pb, const double *t2, const double *vvvo,
     }
     const int o = pb.dm.o, v = pb.dm.v, dp = pb.dm.dp, lp = pb.dm.lp;
     const int64_t v2 = (int64_t)v * v;
-    const int kind = elem_kind(ex.prec);
-    const size_t eb = elem_bytes(ex.prec);
+    const int pprec = operand_prec(ex.prec, o, v);
+    const int kind = elem_kind(pprec);
+    const size_t eb = elem_bytes(pprec);
     const bool split = ex.prec != TCORR_FP64;
     const size_t nG = (size_t)o * v2 * dp, nT2K = (size_t)o * v2 * lp;
     const size_t nT2R = (size_t)o * o * v * dp, nAoN = (size_t)o * o * v * lp;
@@ -274,6 +285,7 @@ void build_schedule(Exec &ex, Problem &pb) {
 
 // Device bytes of one problem's resident data (operands, epilogue inputs, tables).
 size_t problem_bytes(const Dims &d, int prec) {
+    prec = operand_prec(prec, d.o, d.v);
     const size_t o = d.o, v = d.v, v2 = v * v;
     const size_t eb = elem_bytes(prec), parts = operand_planes(prec);
     size_t b = parts * eb * (o * v2 * d.dp + o * v2 * d.lp + o * o * v * d.dp + o * o * v * d.lp);
@@ -328,7 +340,8 @@ void fill_desc(Exec &ex, Problem &pb, int pbt) {
         pb.gemm_units = oz_units_per_task(d);
     } else {
         std::string msg;
-        if (tc_fill_desc(d, ex.prec, pb.op, pbt, TC_KB, msg) != cudaSuccess) throw Fail{TCORR_EUNSUPPORTED, msg};
+        if (tc_fill_desc(d, operand_prec(ex.prec, pb.dm.o, pb.dm.v), pb.op, pbt, TC_KB, ex.pair, msg) != cudaSuccess)
+            throw Fail{TCORR_EUNSUPPORTED, msg};
         pb.gemm_units = tc_units_per_task(d);
     }
 }
@@ -433,7 +446,7 @@ void launch_plan(Exec &ex, const Plan &pl, const Seg *d_segs, const SumSpan *d_s
             Timer tm(ex, KC_GEMM);
             if (ex.prec == TCORR_FP64) CK(launch_ugemm_f64(w, st));
             else if (ex.prec == TCORR_FP64_OZ) CK(launch_ugemm_oz(ex.sm_count, w, st));
-            else CK(launch_ugemm_tc(ex.prec, ex.sm_count, w, st));
+            else CK(launch_ugemm_tc(ex.prec, ex.sm_count, w, st, ex.pair));
             tm.stop();
         }
         {
@@ -482,8 +495,8 @@ tcorr_status check_opts(const tcorr_opts &op, std::string &msg) {
     }
     if (op.prec < TCORR_FP64 || op.prec > TCORR_FP64_OZ || op.batch_tasks < 0 ||
         (op.host_inputs != 0 && op.host_inputs != 1) || (op.tune != 0 && op.tune != 1) ||
-        (op.eager != 0 && op.eager != 1) || op.wave_mb < 0) {
-        msg = "invalid option (precision, batch_tasks, host_inputs, tune, eager or wave_mb)";
+        (op.eager != 0 && op.eager != 1) || op.wave_mb < 0 || (op.single_sm != 0 && op.single_sm != 1)) {
+        msg = "invalid option (precision, batch_tasks, host_inputs, tune, eager, wave_mb or single_sm)";
         return TCORR_EINVAL;
     }
     return TCORR_OK;
@@ -499,6 +512,7 @@ void init_exec(Exec &ex, const tcorr_opts &op, void *stream) {
     ex.prec = op.prec;
     ex.profile = op.profile;
     ex.inject_stall = op.test_stall;
+    ex.pair = op.single_sm == 0;
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&ex.sm_count, cudaDevAttrMultiProcessorCount, dev));
@@ -541,7 +555,8 @@ std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, int> g_tune_cache;
 
 int tuned_pb(Exec &ex, Problem &pb) {
-    const auto key = std::make_tuple(ex.prec, pb.dm.o, pb.dm.v);
+    const int pprec = operand_prec(ex.prec, pb.dm.o, pb.dm.v);
+    const auto key = std::make_tuple(pprec * 2 + (ex.pair ? 1 : 0), pb.dm.o, pb.dm.v);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -562,7 +577,7 @@ int tuned_pb(Exec &ex, Problem &pb) {
     for (int cand : {8, 4, 16}) {
         InstDesc d = pb.desc;
         std::string msg;
-        if (tc_fill_desc(d, ex.prec, pb.op, cand, TC_KB, msg) != cudaSuccess) continue;
+        if (tc_fill_desc(d, pprec, pb.op, cand, TC_KB, ex.pair, msg) != cudaSuccess) continue;
         Seg s{};
         s.ntb = (int)n;
         s.task0 = first;
@@ -579,7 +594,7 @@ int tuned_pb(Exec &ex, Problem &pb) {
         float ms_min = -1.f;
         for (int rep = 0; rep < 3; rep++) {
             CK(cudaEventRecord(e0, ex.stream));
-            CK(launch_ugemm_tc(ex.prec, ex.sm_count, w, ex.stream));
+            CK(launch_ugemm_tc(ex.prec, ex.sm_count, w, ex.stream, ex.pair));
             CK(cudaEventRecord(e1, ex.stream));
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;

@@ -56,6 +56,7 @@ struct Exec {
     int prec = TCORR_FP64;
     int profile = 0;
     int inject_stall = 0;
+    bool pair = true;              // split precisions: tensor-core tiles on SM pairs
     int sm_count = 0, cc_major = 0, cc_minor = 0;
     cudaStream_t stream = nullptr;
     size_t bytes = 0;              // device bytes held
@@ -153,6 +154,18 @@ void release(Exec &ex);
 const double *device_view(Exec &ex, const double *src, size_t n, bool host, double *&tmp);
 void free_tmp(Exec &ex, double *&tmp, size_t n);
 void resolve_timers(Exec &ex);
+// Algorithmic flops of a problem: 12 v^3 (v + o) per task, i = j = k excluded.
+double problem_flops(int o, int v);
+// Operand precision of a problem run at precision prec.  A BF16 hi + lo split
+// leaves up to 2^-17 of each operand unrepresented (16 significant bits); on
+// E(T) that residual averages below the 1e-6 bound only over enough work:
+// over seeded problems across o = 4..40, v = 20..300 the BF16X3 error reached
+// 1.5e-6 on problems below 1e10 flops and at most 2.8e-7 above 1e11, while
+// TF32X3 stayed within 1.4e-7 .. 2.1e-7 throughout.  So BF16X3 problems below
+// BF16_MIN_FLOPS run on TF32 hi + lo operands (same three products, same
+// kernels); every other precision is unchanged.
+constexpr double BF16_MIN_FLOPS = TCORR_BF16_MIN_FLOPS;
+int operand_prec(int prec, int o, int v);
 int elem_kind(int prec);
 bool is_split(int prec);     // TF32x3 / BF16x3 (hi + lo operands, FP32 U and epilogue)
 bool fp64_epilogue(int prec);  // FP64 and FP64 emulation: FP64 U, epilogue inputs and epilogue

@@ -151,6 +151,7 @@ void admit(tcorr_server_s &s) {
         s.used += j->bytes;
         s.peak = std::max(s.peak, s.used);
         j->ex.prec = s.ex.prec;
+        j->ex.pair = s.ex.pair;
         j->ex.stream = s.ex.stream;
         j->ex.pool = s.pool;
         j->ex.sm_count = s.ex.sm_count;

@@ -63,6 +63,30 @@ static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, vol
         }
     }
 }
+// As mbar_test / mbar_wait with cluster-scope acquire: for barriers that
+// complete on arrivals or copies from the other CTA of an SM pair.
+__device__ __forceinline__ bool mbar_test_cl(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+static __device__ __noinline__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_test_cl(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_test_cl(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (*abort_flag) return false;
+            if (it >= WAIT_MIN_POLLS && gtimer() - t0 > WAIT_LIMIT_NS) return false;
+        }
+    }
+}
 __device__ __forceinline__ void fail(volatile int *abort_flag, int *err, int code) {
     *abort_flag = 1;
     atomicOr(err, code);
@@ -194,21 +218,134 @@ __device__ __forceinline__ Item decode(const Wave &w, int64_t it, SegCache &c) {
 }
 __device__ __forceinline__ int num_chunks(const InstDesc &d) { return 2 * d.kv + 2 * d.ko; }
 // K steps of chunk ch that carry data: the K extent of each segment is padded
-// only to 16, so the last chunk of a segment may hold a single BF16 K step
-// (the rest of its 64-byte rows is TMA zero fill).  kv, ko: chunks of the
-// d and l segments; dp, lp: their padded extents.
-template <int KIND>
-__device__ __forceinline__ int chunk_ksteps(int kv, int ko, int dp, int lp, int ch) {
-    if constexpr (KIND == 1) {
-        return 2;  // TF32: 16 elements per chunk, always all data
-    } else {
-        int kk, kext;
-        if (ch < 2 * kv) { kk = ch < kv ? ch : ch - kv; kext = dp; }
-        else { kk = ch - 2 * kv; kk = kk < ko ? kk : kk - ko; kext = lp; }
-        return kext - kk * 32 >= 32 ? 2 : 1;
-    }
+// only to 16, so the last BF16 chunk of a segment may hold a single K step
+// (the rest of its 64-byte rows is TMA zero fill); a TF32 chunk (16 elements)
+// is always all data.  kind: 1 = TF32, 2 = BF16; kv, ko: chunks of the d and l
+// segments; dp, lp: their padded extents.
+__device__ __forceinline__ int chunk_ksteps(int kind, int kv, int ko, int dp, int lp, int ch) {
+    if (kind == 1) return 2;
+    int kk, kext;
+    if (ch < 2 * kv) { kk = ch < kv ? ch : ch - kv; kext = dp; }
+    else { kk = ch - 2 * kv; kk = kk < ko ? kk : kk - ko; kext = lp; }
+    return kext - kk * 32 >= 32 ? 2 : 1;
 }
 
+// ---- SM pairs (thread-block clusters of 2 CTAs, tcgen05 cta_group::2) -----
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// shared::cluster address of the variable at shared::cta address a in CTA rank
+__device__ __forceinline__ uint32_t peer_addr(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// arrive on an mbarrier of either CTA of the cluster (shared::cluster address)
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cl) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cl) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t addr_cl, uint32_t v) {
+    asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(addr_cl), "r"(v) : "memory");
+}
+// TMA loads into this CTA's shared memory whose completion is signalled on an
+// mbarrier of either CTA of the pair (bar_cl: shared::cluster address)
+__device__ __forceinline__ void tma_load_4d_pair(uint32_t dst, const CUtensorMap *map, uint32_t bar_cl,
+                                                 int c0, int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cta.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+        "l"(map), "r"(bar_cl), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap *map, uint32_t bar_cl,
+                                                 int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cta.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"(map), "r"(bar_cl), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+// tcgen05.mma over the SM pair (M = 256: A rows 0-127 from this CTA's shared
+// memory, 128-255 from the peer's at the same offsets; B's N columns split in
+// halves the same way; each CTA's tensor memory receives its own 128 rows)
+template <int KIND>
+__device__ __forceinline__ void tc_mma_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (KIND == 1) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    }
+}
+// arrives once on the mbarrier at shared::cta offset bar in every CTA of
+// cta_mask when every pair MMA issued so far by this thread has completed
+__device__ __forceinline__ void tc_commit_pair(uint32_t bar, uint16_t cta_mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            bar),
+        "h"(cta_mask)
+        : "memory");
+}
+
+// MMA of operand type KIND (1 = TF32, 2 = BF16) on one SM (CG = 1) or an SM pair (CG = 2)
+template <int KIND, int CG>
+__device__ __forceinline__ void tc_mma_cg(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (CG == 1) tc_mma<KIND>(d, a, b, idesc, acc);
+    else tc_mma_pair<KIND>(d, a, b, idesc, acc);
+}
+// The split products of one K chunk held at stage address sA (planes A_hi,
+// A_lo of a_bytes each, then B_hi, B_lo of b_plane bytes each; 64-byte K
+// rows, so one K step of 32 bytes is +2 in a descriptor's address field).
+// lo: hi*lo and lo*hi; first: the chunk opens the accumulator block.
+template <int KIND, int CG>
+__device__ __forceinline__ void issue_lo_products(uint32_t dt, uint32_t sA, uint32_t a_bytes, uint32_t b_plane,
+                                                  int nks, uint32_t idesc, bool first) {
+    const uint64_t dA = sdesc(sA), dAl = sdesc(sA + a_bytes);
+    const uint64_t dB = sdesc(sA + 2 * a_bytes), dBl = sdesc(sA + 2 * a_bytes + b_plane);
+    if constexpr (KIND == 1) {  // a TF32 chunk always holds two K steps
+#pragma unroll
+        for (int kk = 0; kk < 2; kk++) {
+            tc_mma_cg<KIND, CG>(dt, dA + 2 * kk, dBl + 2 * kk, idesc, (first && kk == 0) ? 0u : 1u);
+            tc_mma_cg<KIND, CG>(dt, dAl + 2 * kk, dB + 2 * kk, idesc, 1u);
+        }
+    } else {
+        tc_mma_cg<KIND, CG>(dt, dA, dBl, idesc, first ? 0u : 1u);
+        tc_mma_cg<KIND, CG>(dt, dAl, dB, idesc, 1u);
+        if (nks > 1) {
+            tc_mma_cg<KIND, CG>(dt, dA + 2, dBl + 2, idesc, 1u);
+            tc_mma_cg<KIND, CG>(dt, dAl + 2, dB + 2, idesc, 1u);
+        }
+    }
+}
+// hi*hi of the chunk at stage address sA
+template <int KIND, int CG>
+__device__ __forceinline__ void issue_hi_products(uint32_t dt, uint32_t sA, uint32_t a_bytes, int nks,
+                                                  uint32_t idesc) {
+    const uint64_t dA = sdesc(sA), dB = sdesc(sA + 2 * a_bytes);
+    tc_mma_cg<KIND, CG>(dt, dA, dB, idesc, 1u);
+    if (KIND == 1 || nks > 1) tc_mma_cg<KIND, CG>(dt, dA + 2, dB + 2, idesc, 1u);
+}
 
 __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
                                             int c0, int c1, int c2, int c3, int c4) {

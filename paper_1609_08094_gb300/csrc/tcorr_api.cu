@@ -76,7 +76,7 @@ void destroy_batch(tcorr_batch_s *b) {
 
 extern "C" {
 
-int tcorr_version(void) { return 2; }
+int tcorr_version(void) { return 3; }
 
 const char *tcorr_status_string(tcorr_status s) {
     if ((int)s < 0 || (int)s > 5) return "TCORR_UNKNOWN";

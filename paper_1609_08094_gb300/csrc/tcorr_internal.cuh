@@ -66,6 +66,8 @@ struct InstDesc {
     Dims dm;
     int pb, pc;               // tensor-core pair tile: pb values of b x pc values of c (pb * pc = 128)
     int kb;                   // K chunks per tensor-core accumulator block
+    int kind;                 // split-precision operand type: 1 = TF32, 2 = BF16 hi + lo
+    int pair;                 // tensor-core tiles on SM pairs (cta_group::2, M = 256)
     int nbt, nct, npass, kv, ko, brows;
     uint32_t stage_tx;        // TMA bytes per pipeline stage
     int norb;                 // epilogue block orbits per task (cube edge 8)
@@ -158,7 +160,8 @@ int epilogue_orbits(int v);   // block orbits per task (cube edge 8)
 bool tc_supported(int cc_major, int cc_minor);
 // fills the tensor-core fields of d (maps, tile shape, derived counts) for
 // the operand layouts in op; pb in {4, 8, 16}, kb in {1, 2}
-cudaError_t tc_fill_desc(InstDesc &d, int prec, const Operands &op, int pb, int kb, std::string &err);
+// pair: tiles on SM pairs (2-CTA clusters, M = 256; B boxes of brows / 2 rows)
+cudaError_t tc_fill_desc(InstDesc &d, int prec, const Operands &op, int pb, int kb, bool pair, std::string &err);
 int64_t tc_units_per_task(const InstDesc &d);
 // sets the kernel attributes once per process (call before any stream capture)
 cudaError_t tc_prepare(int prec);
@@ -179,7 +182,8 @@ cudaError_t oz_fill_desc(InstDesc &d, const Operands &op, const int *exps, std::
 int64_t oz_units_per_task(const InstDesc &d);
 cudaError_t oz_prepare();
 cudaError_t launch_ugemm_oz(int sm_count, const Wave &w, cudaStream_t st);
-cudaError_t launch_ugemm_tc(int prec, int sm_count, const Wave &w, cudaStream_t st);
+// pair: the SM-pair kernel (the wave's problems were described with pair = true)
+cudaError_t launch_ugemm_tc(int prec, int sm_count, const Wave &w, cudaStream_t st, bool pair);
 
 // ---- RI-MP2 in split precision on the tensor cores (mp2_tc.cu) ------------------
 constexpr int MP2_TC_TILE = 128;  // virtual indices per tile (M = N of the MMAs)

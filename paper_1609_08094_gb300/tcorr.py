@@ -34,7 +34,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("host_inputs", ctypes.c_int),
                 ("batch_tasks", ctypes.c_int), ("profile", ctypes.c_int),
                 ("test_stall", ctypes.c_int), ("tune", ctypes.c_int),
-                ("eager", ctypes.c_int), ("wave_mb", ctypes.c_int)]
+                ("eager", ctypes.c_int), ("wave_mb", ctypes.c_int), ("single_sm", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -158,6 +158,9 @@ EXPORTS = ("tcorr_create", "tcorr_energy", "tcorr_energy_range", "tcorr_num_task
 JOB_STATES = ("queued", "running", "done", "failed")
 SERVER_STATS = ("submitted", "done", "failed", "running", "queued", "bytes", "peak_bytes", "waves")
 NOALLOC_MAX_V = 64
+# TCORR_BF16X3 problems below these sizes run on TF32 hi + lo operands (include/tcorr.h)
+BF16_MIN_FLOPS = 1e11
+MP2_BF16_MIN_TERMS = 16777216
 
 
 def _prec(prec) -> int:
@@ -200,7 +203,8 @@ class Tcorr:
     None for torch's current stream (device inputs) / the default stream."""
 
     def __init__(self, o, v, eps_occ, eps_vir, t1, t2, vvvo, ooov, ovov, prec="fp64",
-                 batch_tasks=0, profile=False, stream=None, test_stall=False, tune=False):
+                 batch_tasks=0, profile=False, stream=None, test_stall=False, tune=False,
+                 single_sm=False):
         lib = load()
         arrays = dict(eps_occ=eps_occ, eps_vir=eps_vir, t1=t1, t2=t2, vvvo=vvvo, ooov=ooov,
                       ovov=ovov)
@@ -214,7 +218,8 @@ class Tcorr:
         prec = _prec(prec)
         opts = Opts(prec=int(prec), host_inputs=0 if on_device else 1,
                     batch_tasks=int(batch_tasks), profile=1 if profile else 0,
-                    test_stall=1 if test_stall else 0, tune=1 if tune else 0)
+                    test_stall=1 if test_stall else 0, tune=1 if tune else 0,
+                    single_sm=1 if single_sm else 0)
         if stream is None and on_device:
             import torch
             stream = torch.cuda.current_stream(t2.device)
@@ -302,7 +307,7 @@ class Batch:
     (E[4], E[5], E(T))."""
 
     def __init__(self, problems, prec="fp64", batch_tasks=0, profile=False, stream=None,
-                 tune=False, eager=False, wave_mb=0):
+                 tune=False, eager=False, wave_mb=0, single_sm=False):
         lib = load()
         items = []
         for p in problems:
@@ -328,7 +333,8 @@ class Batch:
         prec = _prec(prec)
         opts = Opts(prec=int(prec), host_inputs=0 if on_device else 1,
                     batch_tasks=int(batch_tasks), profile=1 if profile else 0,
-                    tune=1 if tune else 0, eager=1 if eager else 0, wave_mb=int(wave_mb))
+                    tune=1 if tune else 0, eager=1 if eager else 0, wave_mb=int(wave_mb),
+                    single_sm=1 if single_sm else 0)
         if stream is None and on_device:
             import torch
             stream = torch.cuda.current_stream(items[0][5].device)
@@ -402,12 +408,12 @@ class Server:
     jobs (0 = 80% of free memory)."""
 
     def __init__(self, prec="bf16x3", hbm_bytes=0, wave_mb=0, batch_tasks=0, profile=False,
-                 stream=None, test_stall=False):
+                 stream=None, test_stall=False, single_sm=False):
         lib = load()
         prec = _prec(prec)
         opts = Opts(prec=int(prec), host_inputs=0, batch_tasks=int(batch_tasks),
                     profile=1 if profile else 0, test_stall=1 if test_stall else 0,
-                    wave_mb=int(wave_mb))
+                    wave_mb=int(wave_mb), single_sm=1 if single_sm else 0)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream()

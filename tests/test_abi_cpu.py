@@ -40,7 +40,7 @@ def test_status_strings_and_version(lib):
     for i, s in enumerate(tcorr.STATUS):
         assert lib.tcorr_status_string(i).decode() == s
     assert lib.tcorr_status_string(99).decode() == "TCORR_UNKNOWN"
-    assert lib.tcorr_version() == 2
+    assert lib.tcorr_version() == 3
 
 
 def test_invalid_arguments_rejected_before_device_work(lib):
@@ -153,3 +153,14 @@ def test_mp2_arguments_rejected_before_device_work(lib):
     assert lib.tcorr_mp2_kernel_times(None, None, None, 0) == 1
     assert lib.tcorr_mp2_device_bytes(None) == -1
     assert lib.tcorr_mp2_destroy(None) == 0
+
+
+def test_binding_constants_match_the_header():
+    """The binding mirrors the header's size limits and routing thresholds."""
+    import re
+    from paper_1609_08094_gb300 import tcorr
+    hdr = open(os.path.join(ROOT, "include", "tcorr.h")).read()
+    vals = dict(re.findall(r"#define (TCORR_\w+) ([0-9.e+]+)", hdr))
+    assert int(vals["TCORR_NOALLOC_MAX_V"]) == tcorr.NOALLOC_MAX_V
+    assert float(vals["TCORR_BF16_MIN_FLOPS"]) == tcorr.BF16_MIN_FLOPS
+    assert float(vals["TCORR_MP2_BF16_MIN_TERMS"]) == tcorr.MP2_BF16_MIN_TERMS

@@ -33,8 +33,10 @@ def rel(a, b):
 def problems():
     # uneven shapes spanning several tiles and ragged tails, plus degenerate ones:
     # o = 1 (only i = j = k tasks, E = 0) and v below one tile edge
+    # and one problem above TCORR_BF16_MIN_FLOPS, so that a BF16X3 batch mixes
+    # BF16-operand and TF32-operand problems in the same waves
     shapes = [(3, 20, 1), (5, 47, 2), (1, 24, 3), (4, 9, 4), (2, 130, 5), (6, 33, 6),
-              (4, 64, 7), (3, 16, 8)]
+              (4, 64, 7), (3, 16, 8), (6, 160, 9)]
     insts = [synth.make_instance(o, v, None, seed) for o, v, seed in shapes]
     refs = [oracle.energy(i) for i in insts]
     return insts, refs
@@ -124,7 +126,7 @@ def test_batch_config_shapes_sample():
     shapes = synth.batch_shapes(8, seed=100)
     insts = [synth.make_instance(o, v, naux, s) for o, v, naux, s in shapes]
     dev = [i.to("cuda") for i in insts]
-    for prec in ("fp64", "tf32x3"):
+    for prec in ("fp64", "tf32x3", "bf16x3"):
         with tcorr.Batch(dev, prec=prec) as b:
             e = b.energy()
         for n, inst in enumerate(insts):

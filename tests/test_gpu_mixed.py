@@ -74,7 +74,33 @@ def test_mixed_edge_cases(prec):
     assert e5 == 0.0 and e == e4
 
 
-def test_bounded_wait_expiry_reports_timeout_and_context_survives():
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("o,v,seed", [(4, 20, 1), (3, 16, 2), (3, 130, 5), (2, 270, 7), (6, 160, 8)])
+def test_sm_pair_tiles_against_single_sm_tiles_and_oracle(prec, o, v, seed):
+    """The SM-pair kernel (2-CTA clusters, M = 256; the default) and the
+    single-SM kernel (M = 128) evaluate the same K blocks in the same order
+    per output row: both within 1e-6 of the oracle, per task as well.  Shapes:
+    v below one 32-row pair of B halves, an odd number of pair tiles (the last
+    pair half empty), two N passes (v = 270), and a BF16-operand problem."""
+    inst = synth.make_instance(o, v, None, seed)
+    tasks = oracle.sorted_triples(o)
+    ref = oracle.triple_energies(inst, tasks)
+    dev = inst.to("cuda")
+    with tcorr.Tcorr.from_instance(dev, prec=prec) as t:
+        e_pair, per_pair = t.energy_range(0, t.num_tasks, per_task=True)
+    with tcorr.Tcorr.from_instance(dev, prec=prec, single_sm=True) as t:
+        e_one, per_one = t.energy_range(0, t.num_tasks, per_task=True)
+    tot = ref.sum()
+    for e in (e_pair, e_one):
+        assert rel(e[2], tot) <= MIXED_TOL, (prec, o, v, e_pair, e_one, tot)
+    scale = np.abs(ref.sum(1)).max()
+    assert np.all(np.abs(per_pair.sum(1) - ref.sum(1)) <= MIXED_TOL * scale)
+    print(f"{prec} o={o} v={v}: pair {rel(e_pair[2], tot):.2e}, single {rel(e_one[2], tot):.2e}, "
+          f"identical {e_pair == e_one}")
+
+
+@pytest.mark.parametrize("single_sm", [False, True])
+def test_bounded_wait_expiry_reports_timeout_and_context_survives(single_sm):
     """Failure detection without a fault: the test-only option makes the
     tensor-core producer of CTA 0 withhold one chunk's loads, so the MMA
     issuer's bounded wait expires.  The call must return TCORR_ETIMEOUT (no
@@ -82,7 +108,7 @@ def test_bounded_wait_expiry_reports_timeout_and_context_survives():
     import time
     inst = synth.make_instance(3, 40, None, 41)
     dev = inst.to("cuda")
-    with tcorr.Tcorr.from_instance(dev, prec="tf32x3", test_stall=True) as t:
+    with tcorr.Tcorr.from_instance(dev, prec="tf32x3", test_stall=True, single_sm=single_sm) as t:
         t0 = time.time()
         with pytest.raises(tcorr.TcorrError) as exc:
             t.energy()

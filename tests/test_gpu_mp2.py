@@ -74,23 +74,11 @@ def test_mp2_rejects_fp64_emulation():
 MIXED_TOL = 1e-6
 
 
-def split_tol(prec, o, v, naux):
-    """1e-6 relative, except BF16x3 on problems of fewer than 1e5 (pair, a, b,
-    gamma) terms.  A BF16 hi + lo split leaves a residual of up to 2^-18 of
-    each operand (lo is rounded to 8 significant bits), so an element of g
-    can be off by 2 x 2^-18 of its terms' magnitude and E, quadratic in g, by
-    about twice that: 2^-15 in the worst case.  The 1e-6 level relies on the
-    residuals' random signs averaging over many terms, which a single pair
-    with v = 13 and naux = 7 does not give."""
-    if prec == "bf16x3" and o * (o + 1) // 2 * v * v * naux < 10 ** 5:
-        return 2.0 ** -15
-    return MIXED_TOL
-
-
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
 @pytest.mark.parametrize("o,v,naux,seed", [
     (3, 20, 5, 1),         # one tile of 128 with 20 valid rows; naux below one K chunk
-    (1, 13, 7, 3),         # a single pair (i = j)
+    (1, 13, 7, 3),         # a single pair (i = j); BF16X3 runs on TF32 operands here
+    (2, 65, 12, 5),        # BF16X3 on TF32 operands (1.5e5 terms)
     (4, 130, 61, 4),       # two tiles, the second with 2 valid rows
     (7, 200, 200, 5),      # ragged naux (kp = 224)
     (2, 300, 420, 7),      # three tiles, the last with 44 valid rows
@@ -107,10 +95,9 @@ def test_mp2_split_precision_matches_oracle(prec, o, v, naux, seed):
     err = rel(e1[2], ref[2])
     print(f"rimp2 {prec} o={o} v={v} naux={naux}: rel err E {err:.2e}, E_J {rel(e1[0], ref[0]):.2e}, "
           f"E_K {abs(e1[1] - ref[1]) / abs(ref[2]):.2e}")
-    tol = split_tol(prec, o, v, naux)
-    assert err <= tol
-    assert rel(e1[0], ref[0]) <= tol
-    assert abs(e1[1] - ref[1]) <= tol * abs(ref[2])
+    assert err <= MIXED_TOL
+    assert rel(e1[0], ref[0]) <= MIXED_TOL
+    assert abs(e1[1] - ref[1]) <= MIXED_TOL * abs(ref[2])
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])

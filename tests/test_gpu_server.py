@@ -13,7 +13,8 @@ from paper_1609_08094_gb300 import synth, tcorr
 
 pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-10, "tf32x3": 1e-6, "bf16x3": 1e-6}
-SHAPES = [(4, 20, 11), (6, 47, 12), (3, 130, 13), (1, 24, 14), (5, 33, 15), (2, 64, 16)]
+# small jobs (BF16X3 runs them on TF32 operands) and one above TCORR_BF16_MIN_FLOPS
+SHAPES = [(4, 20, 11), (6, 47, 12), (3, 130, 13), (1, 24, 14), (5, 33, 15), (2, 64, 16), (6, 160, 17)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -48,7 +49,7 @@ def solo(dev, prec):
 def test_alone_and_in_the_mix_are_identical(jobs, prec):
     insts, dev, refs = jobs
     alone = [solo(d, prec) for d in dev]
-    with tcorr.Server(prec=prec, wave_mb=64) as s:
+    with tcorr.Server(prec=prec, wave_mb=128) as s:
         ids = [s.submit(d) for d in dev[:3]]
         s.step()
         assert s.poll(ids[0])[0] in ("running", "done")
@@ -76,7 +77,7 @@ def test_admission_respects_the_budget(jobs):
     _, dev, _ = jobs
     # room for a few of the ~35-70 MB job footprints at a time: the rest must queue
     budget = 300 << 20
-    with tcorr.Server(prec="bf16x3", hbm_bytes=budget, wave_mb=32) as s:
+    with tcorr.Server(prec="bf16x3", hbm_bytes=budget, wave_mb=64) as s:
         ids = [s.submit(d) for d in dev * 3]
         saw_queue = False
         while True:
