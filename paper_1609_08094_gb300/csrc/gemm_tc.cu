@@ -174,67 +174,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            uint32_t hblk = 0;  // K blocks issued so far: buffer hblk & 1, phase (hblk >> 1) & 1
-            bool ok = true;
+            MmaRing rg;
+            rg.full0 = smem_u32(&bar_full[0]);
+            rg.empty0 = smem_u32(&bar_empty[0]);
+            rg.hfull0 = smem_u32(&bar_hfull[0]);
+            rg.hempty0 = smem_u32(&bar_hempty[0]);
+            rg.lo0 = desc_lo(sbase);
+            rg.step = stage_bytes >> 4;
+            rg.a16 = A_BYTES >> 4;
+            rg.b16 = b_plane >> 4;
+            rg.nst = nst;
+            rg.stage = 0;
+            rg.phase = 0;
+            rg.hblk = 0;
             SegCache sc;
             seg_reset(sc);
-            for (int64_t it = blockIdx.x; it < wv.n_gemm && ok; it += gridDim.x) {
+            for (int64_t it = blockIdx.x; it < wv.n_gemm; it += gridDim.x) {
                 const Item w = decode(wv, it, sc);
                 if (w.diag) continue;
                 const InstDesc &d = *sc.d;
-                // per-item constants in registers: the issue loop reads no memory
-                const int kv = d.kv, ko = d.ko, dp = d.dm.dp, lp = d.dm.lp;
-                const int nch = 2 * kv + 2 * ko, kb = d.kb, kind = d.kind;
+                const int kv = d.kv, ko = d.ko, nch = 2 * kv + 2 * ko, kind = d.kind;
+                const bool dh = kind == 2 && (d.dm.dp & 31) != 0, lh = kind == 2 && (d.dm.lp & 31) != 0;
                 const int nvalid = min(d.brows, d.dm.v - w.n * d.brows);
                 const int N = (nvalid + 15) / 16 * 16;
                 const uint32_t fmt = kind == 1 ? 2u : 1u;
                 const uint32_t idesc = idesc_m | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17);
-                // K blocks of kb chunks: the small hi*lo and lo*hi products of each
-                // chunk are issued as its data lands, the dominant hi*hi products of
-                // the whole block last, so that the truncation of every instruction
-                // acts on the smallest possible accumulator; the block's stages are
-                // released together once its last MMA is issued.
-                for (int c0 = 0; c0 < nch && ok; c0 += kb) {
-                    const int nb = min(kb, nch - c0);
-                    const uint32_t buf = hblk & 1u;
-                    int st0 = stage;
-                    for (int cb = 0; cb < nb; cb++) {
-                        if (!mbar_wait(smem_u32(&bar_full[stage]), phase, &abort_sh)) {
-                            fail(&abort_sh, wv.err, DERR_TIMEOUT_FULL);
-                            ok = false;
-                            break;
-                        }
-                        if (cb == 0 &&
-                            !mbar_wait(smem_u32(&bar_hempty[buf]), ((hblk >> 1) & 1u) ^ 1u, &abort_sh)) {
-                            fail(&abort_sh, wv.err, DERR_TIMEOUT_TMEM);
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t dt = tmem + buf * (uint32_t)BN;
-                        const uint32_t sA = sbase + stage * stage_bytes;
-                        const int nks = chunk_ksteps(kind, kv, ko, dp, lp, c0 + cb);
-                        if (kind == 1) issue_lo_products<1, 1>(dt, sA, A_BYTES, b_plane, nks, idesc, cb == 0);
-                        else issue_lo_products<2, 1>(dt, sA, A_BYTES, b_plane, nks, idesc, cb == 0);
-                        if (++stage == nst) { stage = 0; phase ^= 1u; }
-                    }
-                    if (!ok) break;
-                    const uint32_t dt = tmem + buf * (uint32_t)BN;
-                    // each stage is released (commit: arrives once every MMA issued
-                    // so far has completed) right after its last product is issued
-                    int sj = st0;
-                    for (int cb = 0; cb < nb; cb++) {
-                        const uint32_t sA = sbase + sj * stage_bytes;
-                        const int nks = chunk_ksteps(kind, kv, ko, dp, lp, c0 + cb);
-                        if (kind == 1) issue_hi_products<1, 1>(dt, sA, A_BYTES, nks, idesc);
-                        else issue_hi_products<2, 1>(dt, sA, A_BYTES, nks, idesc);
-                        tc_commit(smem_u32(&bar_empty[sj]));
-                        if (++sj == nst) sj = 0;
-                    }
-                    tc_commit(smem_u32(&bar_hfull[buf]));
-                    hblk++;
+                // the small hi*lo and lo*hi products of each chunk are issued as it
+                // lands, the dominant hi*hi products of the K block last, so that the
+                // truncation of every instruction acts on the smallest possible
+                // accumulator; each stage is released right after its last product
+                int code = 0;
+                const bool good = kind == 1
+                    ? mma_item<1, 1>(rg, tmem, idesc, nch, -1, -1, -1, -1, &abort_sh, &code)
+                    : mma_item<2, 1>(rg, tmem, idesc, nch, dh ? kv - 1 : -1, dh ? 2 * kv - 1 : -1,
+                                     lh ? 2 * kv + ko - 1 : -1, lh ? nch - 1 : -1, &abort_sh, &code);
+                if (!good) {
+                    fail(&abort_sh, wv.err, code);
+                    break;
                 }
             }
         }
@@ -483,7 +459,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_pair_kernel(const __gr
                 const int cb = w.bt * d.pb, cc = w.ct * d.pc, ca = w.n * d.brows + (int)rank * (N / 2);
                 const uint32_t stage_tx = d.stage_tx;  // both CTAs' bytes
                 for (int ch = 0; ch < nch; ch++) {
-                    if (!mbar_wait_cl(smem_u32(&bar_empty[stage]), phase ^ 1u, &abort_sh)) {
+                    if (!mbar_wait(smem_u32(&bar_empty[stage]), phase ^ 1u, &abort_sh)) {
                         fail_pair(&abort_sh, peer_abort, wv.err, DERR_TIMEOUT_EMPTY);
                         ok = false;
                         break;
@@ -526,7 +502,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_pair_kernel(const __gr
                     for (int s = 0; s < nst; s++) {
                         if (last_phase[s] < 0) continue;
                         const uint64_t t0 = gtimer();
-                        while (!mbar_test_cl(smem_u32(&bar_full[s]), (uint32_t)last_phase[s]) &&
+                        while (!mbar_test(smem_u32(&bar_full[s]), (uint32_t)last_phase[s]) &&
                                gtimer() - t0 < WAIT_LIMIT_NS) {
                         }
                     }
@@ -536,68 +512,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_pair_kernel(const __gr
         }
     } else if (warp == 1) {
         if (lane == 0 && leader) {
-            int stage = 0;
-            uint32_t phase = 0;
-            uint32_t hblk = 0;
-            bool ok = true;
+            MmaRing rg;
+            rg.full0 = smem_u32(&bar_full[0]);
+            rg.empty0 = smem_u32(&bar_empty[0]);
+            rg.hfull0 = smem_u32(&bar_hfull[0]);
+            rg.hempty0 = smem_u32(&bar_hempty[0]);
+            rg.lo0 = desc_lo(sbase);
+            rg.step = stage_bytes >> 4;
+            rg.a16 = A_BYTES >> 4;
+            rg.b16 = b_plane >> 4;
+            rg.nst = nst;
+            rg.stage = 0;
+            rg.phase = 0;
+            rg.hblk = 0;
             SegCache sc;
             seg_reset(sc);
-            for (int64_t it = cid; it < wv.n_gemm && ok; it += ncl) {
+            for (int64_t it = cid; it < wv.n_gemm; it += ncl) {
                 const PairItem pw = decode_pair(wv, it, sc, rank);
                 const Item &w = pw.it;
                 if (w.diag) continue;
                 const InstDesc &d = *sc.d;
-                const int kv = d.kv, ko = d.ko, dp = d.dm.dp, lp = d.dm.lp;
-                const int nch = 2 * kv + 2 * ko, kb = d.kb, kind = d.kind;
+                const int kv = d.kv, ko = d.ko, nch = 2 * kv + 2 * ko, kind = d.kind;
+                const bool dh = kind == 2 && (d.dm.dp & 31) != 0, lh = kind == 2 && (d.dm.lp & 31) != 0;
                 const int nvalid = min(d.brows, d.dm.v - w.n * d.brows);
                 const int N = (nvalid + 15) / 16 * 16;
                 const uint32_t fmt = kind == 1 ? 2u : 1u;
                 const uint32_t idesc = idesc_m | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17);
-                // the same K-block order as the single-SM kernel: small products
-                // of each chunk as it lands, the block's hi*hi products last
-                for (int c0 = 0; c0 < nch && ok; c0 += kb) {
-                    const int nb = min(kb, nch - c0);
-                    const uint32_t buf = hblk & 1u;
-                    int st0 = stage;
-                    for (int cb = 0; cb < nb; cb++) {
-                        if (!mbar_wait_cl(smem_u32(&bar_full[stage]), phase, &abort_sh)) {
-                            fail_pair(&abort_sh, peer_abort, wv.err, DERR_TIMEOUT_FULL);
-                            ok = false;
-                            break;
-                        }
-                        if (cb == 0 &&
-                            !mbar_wait_cl(smem_u32(&bar_hempty[buf]), ((hblk >> 1) & 1u) ^ 1u, &abort_sh)) {
-                            fail_pair(&abort_sh, peer_abort, wv.err, DERR_TIMEOUT_TMEM);
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t dt = tmem + buf * (uint32_t)BN;
-                        const uint32_t sA = sbase + stage * stage_bytes;
-                        const int nks = chunk_ksteps(kind, kv, ko, dp, lp, c0 + cb);
-                        if (kind == 1) issue_lo_products<1, 2>(dt, sA, A_BYTES, b_plane, nks, idesc, cb == 0);
-                        else issue_lo_products<2, 2>(dt, sA, A_BYTES, b_plane, nks, idesc, cb == 0);
-                        if (++stage == nst) { stage = 0; phase ^= 1u; }
-                    }
-                    if (!ok) break;
-                    const uint32_t dt = tmem + buf * (uint32_t)BN;
-                    int sj = st0;
-                    for (int cb = 0; cb < nb; cb++) {
-                        const uint32_t sA = sbase + sj * stage_bytes;
-                        const int nks = chunk_ksteps(kind, kv, ko, dp, lp, c0 + cb);
-                        if (kind == 1) issue_hi_products<1, 2>(dt, sA, A_BYTES, nks, idesc);
-                        else issue_hi_products<2, 2>(dt, sA, A_BYTES, nks, idesc);
-                        tc_commit_pair(smem_u32(&bar_empty[sj]), (uint16_t)3);
-                        if (++sj == nst) sj = 0;
-                    }
-                    tc_commit_pair(smem_u32(&bar_hfull[buf]), (uint16_t)3);
-                    hblk++;
+                int code = 0;
+                const bool good = kind == 1
+                    ? mma_item<1, 2>(rg, tmem, idesc, nch, -1, -1, -1, -1, &abort_sh, &code)
+                    : mma_item<2, 2>(rg, tmem, idesc, nch, dh ? kv - 1 : -1, dh ? 2 * kv - 1 : -1,
+                                     lh ? 2 * kv + ko - 1 : -1, lh ? nch - 1 : -1, &abort_sh, &code);
+                if (!good) {
+                    fail_pair(&abort_sh, peer_abort, wv.err, code);
+                    break;
                 }
             }
             // every MMA issued by this thread has completed before the pair tears down
             tc_commit_pair(smem_u32(&bar_fin), (uint16_t)1);
             const uint64_t t0 = gtimer();
-            while (!mbar_test_cl(smem_u32(&bar_fin), 0u) && gtimer() - t0 < WAIT_LIMIT_NS) {
+            while (!mbar_test(smem_u32(&bar_fin), 0u) && gtimer() - t0 < WAIT_LIMIT_NS) {
             }
         }
     } else {
@@ -633,7 +587,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_pair_kernel(const __gr
             for (int hb = 0; hb < nhb; hb++) {
                 const uint32_t buf = hblk & 1u;
                 int good = 1;
-                if (lane == 0) good = mbar_wait_cl(smem_u32(&bar_hfull[buf]), (hblk >> 1) & 1u, &abort_sh) ? 1 : 0;
+                if (lane == 0) good = mbar_wait(smem_u32(&bar_hfull[buf]), (hblk >> 1) & 1u, &abort_sh) ? 1 : 0;
                 good = __shfl_sync(0xffffffffu, good, 0);
                 __syncwarp();
                 if (!good) { ok = false; break; }
@@ -708,8 +662,8 @@ cudaError_t tc_fill_desc(InstDesc &d, int prec, const Operands &op, int pb, int 
         err = "tensor-core pair tile: pb must be 4, 8 or 16";
         return cudaErrorInvalidValue;
     }
-    if (kb < 1 || kb > 3) {  // a K block holds its stages until its last MMA (>= 4 stages)
-        err = "tensor-core accumulator block: kb must be 1 .. 3";
+    if (kb != 2) {  // the MMA issuer works in K blocks of two chunks (mma_item)
+        err = "tensor-core accumulator block: kb must be 2";
         return cudaErrorInvalidValue;
     }
     const int o = d.dm.o, v = d.dm.v, dp = d.dm.dp, lp = d.dm.lp;
@@ -726,8 +680,9 @@ cudaError_t tc_fill_desc(InstDesc &d, int prec, const Operands &op, int pb, int 
     d.nbt = (v + pb - 1) / pb;
     d.nct = (v + pc - 1) / pc;
     d.npass = (v + BN - 1) / BN;
-    // pass width: <= BN, a multiple of 16 (single SM) or of 32 (SM pair: the pair
-    // MMA's N is a multiple of 32, each SM holding N / 2 rows of B)
+    // pass width: <= BN, a multiple of 16 (single SM) or of 32 (SM pair: each SM
+    // holds brows / 2 rows of B, a multiple of 16; the MMA's N is the pass's valid
+    // width rounded to 16, the peer's half starting at N / 2, a multiple of 8)
     const int wq = pair ? 32 : 16;
     d.brows = round_up((v + d.npass - 1) / d.npass, wq);
     d.kv = (v + kch - 1) / kch;

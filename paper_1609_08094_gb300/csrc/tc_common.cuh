@@ -63,30 +63,6 @@ static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, vol
         }
     }
 }
-// As mbar_test / mbar_wait with cluster-scope acquire: for barriers that
-// complete on arrivals or copies from the other CTA of an SM pair.
-__device__ __forceinline__ bool mbar_test_cl(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-static __device__ __noinline__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-    if (mbar_test_cl(bar, parity)) return true;
-    const uint64_t t0 = gtimer();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_test_cl(bar, parity)) return true;
-        if ((it & 63) == 0) {
-            if (*abort_flag) return false;
-            if (it >= WAIT_MIN_POLLS && gtimer() - t0 > WAIT_LIMIT_NS) return false;
-        }
-    }
-}
 __device__ __forceinline__ void fail(volatile int *abort_flag, int *err, int code) {
     *abort_flag = 1;
     atomicOr(err, code);
@@ -256,9 +232,13 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-// arrive on an mbarrier of either CTA of the cluster (shared::cluster address)
+// arrive on an mbarrier of either CTA of the cluster (shared::cluster
+// address).  Default (CTA-scope release) semantics: the hand-offs it signals
+// are tensor-memory reads, ordered by tcgen05 fences around the barrier; a
+// cluster-scope release would also wait for this thread's earlier global
+// stores (the U rows), which the other CTA never reads.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cl) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cl) : "memory");
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar_cl) : "memory");
 }
 __device__ __forceinline__ void st_cluster_u32(uint32_t addr_cl, uint32_t v) {
     asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(addr_cl), "r"(v) : "memory");
@@ -308,43 +288,119 @@ __device__ __forceinline__ void tc_commit_pair(uint32_t bar, uint16_t cta_mask) 
         : "memory");
 }
 
-// MMA of operand type KIND (1 = TF32, 2 = BF16) on one SM (CG = 1) or an SM pair (CG = 2)
-template <int KIND, int CG>
-__device__ __forceinline__ void tc_mma_cg(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    if constexpr (CG == 1) tc_mma<KIND>(d, a, b, idesc, acc);
-    else tc_mma_pair<KIND>(d, a, b, idesc, acc);
+// ---- lean MMA issue ---------------------------------------------------------
+// One thread issues every MMA of a CTA (or of an SM pair), and between two
+// MMAs it runs a few dependent instructions of its own, each several clocks
+// long: at M = 128, N = 256, K = 16 an MMA is ~128 tensor clocks, so the
+// issue path has to stay near ten instructions per MMA.  Descriptors are
+// therefore kept as their low 32-bit word (start address >> 4 and the LBO
+// field; one K step of 32 bytes is +2), paired with a constant high word in
+// the asm, and the accumulate flag is a compile-time constant.
+constexpr uint32_t DESC_LO_FLAGS = 1u << 16;                 // LBO = 1 (unused for swizzled K-major tiles)
+constexpr uint32_t DESC_HI = 32u | (1u << 14) | (4u << 29);  // SBO = 512 bytes, bit 46, 64-byte swizzle
+static_assert(((uint64_t)DESC_HI << 32 | DESC_LO_FLAGS) == (((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+                                                             ((uint64_t)1 << 46) | ((uint64_t)4 << 61)),
+              "same descriptor fields as sdesc");
+__device__ __forceinline__ uint32_t desc_lo(uint32_t addr) { return ((addr & 0x3FFFFu) >> 4) | DESC_LO_FLAGS; }
+
+#define TCX_MMA_ASM(CGS, KINDS, PRED)                                                             \
+    asm volatile("{\n\t.reg .b64 da, db;\n\t.reg .pred p;\n\t"                                  \
+                 "mov.b64 da, {%1, %4};\n\tmov.b64 db, {%2, %4};\n\t" PRED                      \
+                 "tcgen05.mma.cta_group::" CGS ".kind::" KINDS " [%0], da, db, %3, p;\n\t}\n" ::"r"(d), \
+                 "r"(a_lo), "r"(b_lo), "r"(idesc), "r"(DESC_HI))
+template <int KIND, int CG, bool ACC>
+__device__ __forceinline__ void mma_lo(uint32_t d, uint32_t a_lo, uint32_t b_lo, uint32_t idesc) {
+    if constexpr (CG == 1 && KIND == 1 && ACC) TCX_MMA_ASM("1", "tf32", "setp.eq.u32 p, 0, 0;\n\t");
+    else if constexpr (CG == 1 && KIND == 1) TCX_MMA_ASM("1", "tf32", "setp.ne.u32 p, 0, 0;\n\t");
+    else if constexpr (CG == 1 && ACC) TCX_MMA_ASM("1", "f16", "setp.eq.u32 p, 0, 0;\n\t");
+    else if constexpr (CG == 1) TCX_MMA_ASM("1", "f16", "setp.ne.u32 p, 0, 0;\n\t");
+    else if constexpr (KIND == 1 && ACC) TCX_MMA_ASM("2", "tf32", "setp.eq.u32 p, 0, 0;\n\t");
+    else if constexpr (KIND == 1) TCX_MMA_ASM("2", "tf32", "setp.ne.u32 p, 0, 0;\n\t");
+    else if constexpr (ACC) TCX_MMA_ASM("2", "f16", "setp.eq.u32 p, 0, 0;\n\t");
+    else TCX_MMA_ASM("2", "f16", "setp.ne.u32 p, 0, 0;\n\t");
 }
-// The split products of one K chunk held at stage address sA (planes A_hi,
-// A_lo of a_bytes each, then B_hi, B_lo of b_plane bytes each; 64-byte K
-// rows, so one K step of 32 bytes is +2 in a descriptor's address field).
-// lo: hi*lo and lo*hi; first: the chunk opens the accumulator block.
-template <int KIND, int CG>
-__device__ __forceinline__ void issue_lo_products(uint32_t dt, uint32_t sA, uint32_t a_bytes, uint32_t b_plane,
-                                                  int nks, uint32_t idesc, bool first) {
-    const uint64_t dA = sdesc(sA), dAl = sdesc(sA + a_bytes);
-    const uint64_t dB = sdesc(sA + 2 * a_bytes), dBl = sdesc(sA + 2 * a_bytes + b_plane);
-    if constexpr (KIND == 1) {  // a TF32 chunk always holds two K steps
-#pragma unroll
-        for (int kk = 0; kk < 2; kk++) {
-            tc_mma_cg<KIND, CG>(dt, dA + 2 * kk, dBl + 2 * kk, idesc, (first && kk == 0) ? 0u : 1u);
-            tc_mma_cg<KIND, CG>(dt, dAl + 2 * kk, dB + 2 * kk, idesc, 1u);
-        }
-    } else {
-        tc_mma_cg<KIND, CG>(dt, dA, dBl, idesc, first ? 0u : 1u);
-        tc_mma_cg<KIND, CG>(dt, dAl, dB, idesc, 1u);
-        if (nks > 1) {
-            tc_mma_cg<KIND, CG>(dt, dA + 2, dBl + 2, idesc, 1u);
-            tc_mma_cg<KIND, CG>(dt, dAl + 2, dB + 2, idesc, 1u);
-        }
+#undef TCX_MMA_ASM
+
+// Barriers and ring state of the MMA issuer (shared::cta addresses).
+struct MmaRing {
+    uint32_t full0, empty0, hfull0, hempty0;  // first barrier of each array (8 bytes apart)
+    uint32_t lo0, step;                       // desc_lo of stage 0's A_hi plane; stage stride >> 4
+    uint32_t a16, b16;                        // plane sizes >> 4: A (A_hi -> A_lo), B (B_hi -> B_lo)
+    int nst;
+    int stage;
+    uint32_t phase, hblk;
+};
+// Inline fast path of a bounded wait.
+__device__ __forceinline__ bool wait_fast(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    return mbar_test(bar, parity) || mbar_wait(bar, parity, abort_flag);
+}
+template <int CG>
+__device__ __forceinline__ void commit_to(uint32_t bar) {
+    if constexpr (CG == 1) tc_commit(bar);
+    else tc_commit_pair(bar, (uint16_t)3);
+}
+// The split products of one K chunk in stage st: lo = hi*lo + lo*hi, hi = hi*hi.
+// nks = 1: only the first K step holds data (BF16 segment tail).
+template <int KIND, int CG, bool FIRST>
+__device__ __forceinline__ void chunk_lo(const MmaRing &r, int st, uint32_t dt, uint32_t idesc, int nks) {
+    const uint32_t a = r.lo0 + (uint32_t)st * r.step, b = a + 2 * r.a16;
+    mma_lo<KIND, CG, !FIRST>(dt, a, b + r.b16, idesc);
+    mma_lo<KIND, CG, true>(dt, a + r.a16, b, idesc);
+    if (KIND == 1 || nks > 1) {
+        mma_lo<KIND, CG, true>(dt, a + 2, b + r.b16 + 2, idesc);
+        mma_lo<KIND, CG, true>(dt, a + r.a16 + 2, b + 2, idesc);
     }
 }
-// hi*hi of the chunk at stage address sA
 template <int KIND, int CG>
-__device__ __forceinline__ void issue_hi_products(uint32_t dt, uint32_t sA, uint32_t a_bytes, int nks,
-                                                  uint32_t idesc) {
-    const uint64_t dA = sdesc(sA), dB = sdesc(sA + 2 * a_bytes);
-    tc_mma_cg<KIND, CG>(dt, dA, dB, idesc, 1u);
-    if (KIND == 1 || nks > 1) tc_mma_cg<KIND, CG>(dt, dA + 2, dB + 2, idesc, 1u);
+__device__ __forceinline__ void chunk_hi(const MmaRing &r, int st, uint32_t dt, uint32_t idesc, int nks) {
+    const uint32_t a = r.lo0 + (uint32_t)st * r.step, b = a + 2 * r.a16;
+    mma_lo<KIND, CG, true>(dt, a, b, idesc);
+    if (KIND == 1 || nks > 1) mma_lo<KIND, CG, true>(dt, a + 2, b + 2, idesc);
+}
+// Every MMA of one work item: K blocks of two chunks, each into a fresh TMEM
+// accumulator buffer (tmem + 256 * (block & 1)); within a block the small
+// products of each chunk are issued as the chunk lands and the block's hi*hi
+// products last, then each stage is released and the block handed to the
+// drain (see the kernels).  nch: chunks of the item; dtail, ltail: chunk
+// indices of the last chunk of the d and l segments (two each) that hold a
+// single K step (BF16 with the segment's extent 16 mod 32), -1 if none.
+// Returns false (after flagging) when a bounded wait expired.
+template <int KIND, int CG>
+__device__ __forceinline__ bool mma_item(MmaRing &r, uint32_t tmem, uint32_t idesc, int nch, int dt0, int dt1,
+                                         int lt0, int lt1, volatile int *abort_flag, int *fail_code) {
+    for (int c0 = 0; c0 < nch; c0 += 2) {
+        const bool two = c0 + 1 < nch;
+        const uint32_t buf = r.hblk & 1u;
+        const uint32_t dt = tmem + buf * 256u;
+        const int s0 = r.stage;
+        if (!wait_fast(r.full0 + 8u * (uint32_t)s0, r.phase, abort_flag)) { *fail_code = DERR_TIMEOUT_FULL; return false; }
+        if (!wait_fast(r.hempty0 + 8u * buf, ((r.hblk >> 1) & 1u) ^ 1u, abort_flag)) {
+            *fail_code = DERR_TIMEOUT_TMEM;
+            return false;
+        }
+        tc_fence_after();
+        const int n0 = (c0 == dt0 || c0 == dt1 || c0 == lt0 || c0 == lt1) ? 1 : 2;
+        chunk_lo<KIND, CG, true>(r, s0, dt, idesc, n0);
+        if (++r.stage == r.nst) { r.stage = 0; r.phase ^= 1u; }
+        int s1 = -1, n1 = 2;
+        if (two) {
+            s1 = r.stage;
+            if (!wait_fast(r.full0 + 8u * (uint32_t)s1, r.phase, abort_flag)) { *fail_code = DERR_TIMEOUT_FULL; return false; }
+            tc_fence_after();
+            n1 = (c0 + 1 == dt0 || c0 + 1 == dt1 || c0 + 1 == lt0 || c0 + 1 == lt1) ? 1 : 2;
+            chunk_lo<KIND, CG, false>(r, s1, dt, idesc, n1);
+            if (++r.stage == r.nst) { r.stage = 0; r.phase ^= 1u; }
+        }
+        chunk_hi<KIND, CG>(r, s0, dt, idesc, n0);
+        commit_to<CG>(r.empty0 + 8u * (uint32_t)s0);
+        if (two) {
+            chunk_hi<KIND, CG>(r, s1, dt, idesc, n1);
+            commit_to<CG>(r.empty0 + 8u * (uint32_t)s1);
+        }
+        commit_to<CG>(r.hfull0 + 8u * buf);
+        r.hblk++;
+    }
+    return true;
 }
 
 __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, uint32_t bar,

@@ -53,6 +53,7 @@ def test_noalloc_sequence_matches_oracle_and_handle():
              (5, 20, 32, (1, 1, 4)),
              (3, 37, 33, (0, 2, 2)),
              (3, 37, 33, (2, 2, 2))]
+    scale = None
     for o, v, seed, ijk in cases:
         host = synth.make_instance(o, v, None, seed)
         dev = host.to("cuda")
@@ -60,8 +61,10 @@ def test_noalloc_sequence_matches_oracle_and_handle():
         ref = oracle.triple_energies(host, np.array([ijk]))[0]
         if ijk[0] == ijk[1] == ijk[2]:
             assert got[0] == 0.0 and got[1] == 0.0, (ijk, got)  # exact zero, not stale scratch
-            assert ref[0] == 0.0 and ref[1] == 0.0
+            # the oracle sums the literal terms, which cancel to rounding level
+            assert np.all(np.abs(ref) <= FP64_TOL * scale), (ref, scale)
             continue
+        scale = np.abs(ref).max()
         assert np.all(np.abs(got - ref) <= FP64_TOL * np.abs(ref).max()), (o, v, ijk, got, ref)
         with tcorr.Tcorr.from_instance(dev) as t:
             n = [t.task(m) for m in range(t.num_tasks)].index(ijk)
