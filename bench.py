@@ -23,6 +23,7 @@ collective on the data path; the harness reduces timings with max).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -404,14 +405,23 @@ def main():
                        "tcorr_energy_range, 3-double result read, tcorr_destroy"}
         del arrays
 
+    # the main workload's device arrays are not needed by the remaining legs
+    del inst
+    gc.collect()
+    torch.cuda.empty_cache()
+
     # ---- batched: many molecules of uneven size in one graph-replayed launch sequence
     batched = None
     if not args.no_batched:
         batched = bench_batched(args, rank, world, stream)
 
+    gc.collect()
+    torch.cuda.empty_cache()
     serving = None
     if not args.no_serving:
         serving = bench_serving(args, rank, world, stream)
+    gc.collect()
+    torch.cuda.empty_cache()
 
     mp2 = None
     if not args.no_mp2:
@@ -658,7 +668,9 @@ def bench_serving(args, rank, world, stream):
         ids = [srv.submit(window(base, *r)) for r in calib]
         srv.drain()
         calib_s = time.perf_counter() - tc0
-        assert all(srv.poll(i)[0] == "done" for i in ids)
+        bad = [(calib[k][:2], st) for k, (state, _, st) in enumerate(srv.poll(i) for i in ids) if state != "done"]
+        if bad:
+            raise RuntimeError(f"calibration jobs failed ((o, v), status): {bad[:8]}")
         sat = sum(req_flops(o, v) for o, v, _, _ in calib) / calib_s   # flop/s
         lam = cfg["load"] * sat / mean_fl                                # requests/s
         gaps = -np.log(1.0 - synth.uniform(cfg["seed"] + 100 * rank, 30, len(stream_reqs))) / lam

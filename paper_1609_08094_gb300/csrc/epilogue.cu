@@ -50,6 +50,32 @@ __device__ __forceinline__ double recip64(double d, float r0) {
     return fma(r, fma(-d, r, 1.0), r);
 }
 
+// Sum over the CTA of one (E4, E5) pair per thread, in a fixed order, into
+// out[0..1]: the NT pairs through shared memory, NT / 32 per lane of warp 0,
+// then a shuffle tree.  (A shuffle tree over all NT threads would put ten
+// FP64 adds per thread on the FP64 pipe, which bounds these kernels.)
+__device__ __forceinline__ void cta_sum2(double a4, double a5, double (*red)[2], double *out, int tid) {
+    red[tid][0] = a4;
+    red[tid][1] = a5;
+    __syncthreads();
+    if (tid < 32) {
+        double b4 = red[tid][0], b5 = red[tid][1];
+#pragma unroll
+        for (int k = 1; k < NT / 32; k++) {
+            b4 += red[tid + 32 * k][0];
+            b5 += red[tid + 32 * k][1];
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            b4 += __shfl_xor_sync(0xffffffffu, b4, off);
+            b5 += __shfl_xor_sync(0xffffffffu, b5, off);
+        }
+        if (tid == 0) {
+            out[0] = b4;
+            out[1] = b5;
+        }
+    }
+}
+
 // FP64 epilogue; TE: cube edge.  Orbits of three distinct blocks take the
 // element-orbit form (the six orderings of one (a,b,c) share one denominator
 // and the E/O expansion of Z, as in the mixed epilogue), orbits with repeated
@@ -63,7 +89,7 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
     constexpr int NE = TE * TE * TE;         // elements per cube
     __shared__ int comp[6][6];
     __shared__ int distinct[6];
-    __shared__ double red[NT / 32][2];
+    __shared__ double red[NT][2];
 
     const int64_t item = blockIdx.x;
     const Seg sg = wv.segs[seg_find(wv.segs, wv.nseg, item, [](const Seg &x) { return x.epi0; })];
@@ -241,19 +267,7 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
         kahan_add(s4, c4, double(a4));
         kahan_add(s5, c5, double(a5));
     }
-    double r4 = s4 - c4, r5 = s5 - c5;  // fold the compensation
-    for (int off = 16; off > 0; off >>= 1) {
-        r4 += __shfl_xor_sync(0xffffffffu, r4, off);
-        r5 += __shfl_xor_sync(0xffffffffu, r5, off);
-    }
-    if ((tid & 31) == 0) { red[tid >> 5][0] = r4; red[tid >> 5][1] = r5; }
-    __syncthreads();
-    if (tid == 0) {
-        double t4 = 0.0, k4 = 0.0, t5 = 0.0, k5 = 0.0;
-        for (int w = 0; w < NT / 32; w++) { kahan_add(t4, k4, red[w][0]); kahan_add(t5, k5, red[w][1]); }
-        out[0] = t4 - k4;
-        out[1] = t5 - k5;
-    }
+    cta_sum2(s4 - c4, s5 - c5, red, out, tid);  // the compensation folded
 }
 
 
@@ -278,9 +292,9 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
 //    relative error about 1e-7) refined by one Newton-Raphson step
 //    r <- r + r (1 - D r) in FP64 against the FP64 D, which squares the
 //    relative error (below 1e-13);
-//  - numerator x 1/D and every sum from there on (per thread, warp shuffles,
-//    CTA) in FP64; the orbit partials of a task are summed in FP64 (Kahan)
-//    by the task reduction.
+//  - numerator x 1/D and every sum from there on (per thread, then over the
+//    CTA in a fixed order) in FP64; the orbit partials of a task are summed
+//    in FP64 (Kahan) by the task reduction.
 // One Newton step costs two FP64 FMAs per element orbit (per element in the
 // orbits with repeated blocks), so the FP64 pipe (1/64 of the FP32 rate on
 // this part) sees about one instruction per element.
@@ -301,7 +315,7 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
     __shared__ double eijk_s;
     __shared__ int comp[6][6];
     __shared__ int distinct[6];
-    __shared__ double red[NT / 32][2];
+    __shared__ double red[NT][2];
 
     const int64_t item = blockIdx.x;
     const Seg sg = wv.segs[seg_find(wv.segs, wv.nseg, item, [](const Seg &x) { return x.epi0; })];
@@ -505,21 +519,8 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
             }
         }
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        a4 += __shfl_xor_sync(0xffffffffu, a4, off);
-        a5 += __shfl_xor_sync(0xffffffffu, a5, off);
-    }
-    // cross-warp sum in FP64 (8 terms, fixed order); the orbit partials are
-    // summed in FP64 (Kahan) per task
-    if ((tid & 31) == 0) { red[tid >> 5][0] = a4; red[tid >> 5][1] = a5; }
-    __syncthreads();
-    if (tid == 0) {
-        double b4 = 0.0, b5 = 0.0;
-#pragma unroll
-        for (int w = 0; w < NT / 32; w++) { b4 += red[w][0]; b5 += red[w][1]; }
-        out[0] = b4;
-        out[1] = b5;
-    }
+    // the orbit partials of a task are summed in FP64 (Kahan) by the task reduction
+    cta_sum2(a4, a5, red, out, tid);
 }
 #undef OBP
 

@@ -69,6 +69,33 @@ static_assert(OZ_S * 32 * OZ_KB * (1 << (2 * OZ_BETA - 1)) < (1 << 24), "weight 
 static_assert(OZ_HALF % 16 == 0, "the drain loads 16 columns at a time");
 
 
+// The 15 slice products (i + j <= S + 1) of one K chunk into the five weight
+// accumulators (columns t * OZ_N of tmem, t = i + j - 2); a0, b0: descriptor
+// low words of the stage's A and B slice planes.  FIRST: the chunk opens the
+// accumulator block, so each weight's first product zeroes its accumulator.
+template <bool FIRST>
+__device__ __forceinline__ void oz_chunk(uint32_t tmem, uint32_t a0, uint32_t b0, uint32_t idesc, int nks) {
+#pragma unroll
+    for (int t = 0; t < OZ_S; t++) {
+#pragma unroll
+        for (int ia = 0; ia <= t; ia++) {
+            const uint32_t d = tmem + (uint32_t)(t * OZ_N);
+            const uint32_t a = a0 + (uint32_t)((ia * OZ_A) >> 4), b = b0 + (uint32_t)(((t - ia) * OZ_B) >> 4);
+            if (FIRST && ia == 0) mma_lo<2, 1, false>(d, a, b, idesc);
+            else mma_lo<2, 1, true>(d, a, b, idesc);
+        }
+    }
+    if (nks > 1) {
+#pragma unroll
+        for (int t = 0; t < OZ_S; t++) {
+#pragma unroll
+            for (int ia = 0; ia <= t; ia++)
+                mma_lo<2, 1, true>(tmem + (uint32_t)(t * OZ_N), a0 + (uint32_t)((ia * OZ_A) >> 4) + 2,
+                                   b0 + (uint32_t)(((t - ia) * OZ_B) >> 4) + 2, idesc);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(OZ_THREADS, 1) ugemm_oz_kernel(const __grid_constant__ Wave wv) {
     extern __shared__ __align__(1024) uint8_t smem_dyn[];
     __shared__ __align__(8) uint64_t bar_full[OZ_STAGES], bar_empty[OZ_STAGES];
@@ -201,27 +228,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ugemm_oz_kernel(const __grid_co
                         tc_fence_after();
                         const uint32_t sA = sbase + stage * OZ_STAGE, sB = sA + OZ_S * OZ_A;
                         const int nks = chunk_ksteps(2, kv, ko, dp, lp, ch);
-                        // descriptors are linear in the address (its low field is addr >> 4), so every
-                        // plane / K-step descriptor is the stage's base descriptor plus a constant
-                        const uint64_t dA = sdesc(sA), dB = sdesc(sB);
-                        const uint32_t dt0 = tmem;
-#pragma unroll
-                        for (int t = 0; t < OZ_S; t++) {
-                            // the slice pairs of weight t: (i - 1) + (j - 1) = t, both in 0 .. S-1
-                            // (t <= S - 1, so every ia in 0 .. t has jb = t - ia in range)
-#pragma unroll
-                            for (int ia = 0; ia <= t; ia++) {
-#pragma unroll
-                                for (int kk = 0; kk < 2; kk++) {
-                                    if (kk < nks) {
-                                        tc_mma<2>(dt0 + (uint32_t)(t * OZ_N),
-                                                  dA + (uint64_t)((ia * OZ_A + kk * 32) >> 4),
-                                                  dB + (uint64_t)(((t - ia) * OZ_B + kk * 32) >> 4), idesc,
-                                                  (cb == 0 && ia == 0 && kk == 0) ? 0u : 1u);
-                                    }
-                                }
-                            }
-                        }
+                        // descriptor low words (see mma_lo): plane and K-step offsets are
+                        // constants added to the stage's base words.  Every slice product
+                        // is exact in FP32, so their order within a block is free: the
+                        // first K step of every weight first (the block's opening MMA of
+                        // each weight zeroes it), then the second
+                        const uint32_t a0 = desc_lo(sA), b0 = desc_lo(sB);
+                        if (cb == 0) oz_chunk<true>(tmem, a0, b0, idesc, nks);
+                        else oz_chunk<false>(tmem, a0, b0, idesc, nks);
                         tc_commit(smem_u32(&bar_empty[stage]));  // the stage is free once these MMAs are done
                         if (++stage == OZ_STAGES) { stage = 0; phase ^= 1u; }
                     }

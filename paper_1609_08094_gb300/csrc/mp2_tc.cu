@@ -172,23 +172,26 @@ __global__ void __launch_bounds__(MP_THREADS, 1) mp2_tc_kernel(const __grid_cons
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t s = sbase + stage * MP_STAGE;
-                        for (int kk = 0; kk < 2; kk++) {  // two MMA K steps of 32 bytes per chunk
-                            const uint32_t off = kk * 32;
-                            const uint32_t acc = (cb > 0 || kk > 0) ? 1u : 0u;
-                            tc_mma<KIND>(dG, sdesc(s + P_AI_LO * MP_TILE + off), sdesc(s + P_BJ_LO * MP_TILE + off),
-                                         idesc, acc);
-                            tc_mma<KIND>(dG, sdesc(s + P_AI_HI * MP_TILE + off), sdesc(s + P_BJ_LO * MP_TILE + off),
-                                         idesc, 1u);
-                            tc_mma<KIND>(dG, sdesc(s + P_AI_LO * MP_TILE + off), sdesc(s + P_BJ_HI * MP_TILE + off),
-                                         idesc, 1u);
-                            tc_mma<KIND>(dH, sdesc(s + P_AJ_LO * MP_TILE + off), sdesc(s + P_BI_LO * MP_TILE + off),
-                                         idesc, acc);
-                            tc_mma<KIND>(dH, sdesc(s + P_AJ_HI * MP_TILE + off), sdesc(s + P_BI_LO * MP_TILE + off),
-                                         idesc, 1u);
-                            tc_mma<KIND>(dH, sdesc(s + P_AJ_LO * MP_TILE + off), sdesc(s + P_BI_HI * MP_TILE + off),
-                                         idesc, 1u);
-                        }
+                        // descriptor low words of the stage's planes (see mma_lo): one K
+                        // step of 32 bytes is +2; the block's first products zero D
+                        const uint32_t s = desc_lo(sbase + stage * MP_STAGE);
+                        const uint32_t ai = s + P_AI_HI * (MP_TILE >> 4), bj = s + P_BJ_HI * (MP_TILE >> 4);
+                        const uint32_t aj = s + P_AJ_HI * (MP_TILE >> 4), bi = s + P_BI_HI * (MP_TILE >> 4);
+                        constexpr uint32_t LO = MP_TILE >> 4;  // hi plane -> lo plane
+                        if (cb == 0) mma_lo<KIND, 1, false>(dG, ai + LO, bj + LO, idesc);
+                        else mma_lo<KIND, 1, true>(dG, ai + LO, bj + LO, idesc);
+                        mma_lo<KIND, 1, true>(dG, ai, bj + LO, idesc);
+                        mma_lo<KIND, 1, true>(dG, ai + LO, bj, idesc);
+                        if (cb == 0) mma_lo<KIND, 1, false>(dH, aj + LO, bi + LO, idesc);
+                        else mma_lo<KIND, 1, true>(dH, aj + LO, bi + LO, idesc);
+                        mma_lo<KIND, 1, true>(dH, aj, bi + LO, idesc);
+                        mma_lo<KIND, 1, true>(dH, aj + LO, bi, idesc);
+                        mma_lo<KIND, 1, true>(dG, ai + LO + 2, bj + LO + 2, idesc);
+                        mma_lo<KIND, 1, true>(dG, ai + 2, bj + LO + 2, idesc);
+                        mma_lo<KIND, 1, true>(dG, ai + LO + 2, bj + 2, idesc);
+                        mma_lo<KIND, 1, true>(dH, aj + LO + 2, bi + LO + 2, idesc);
+                        mma_lo<KIND, 1, true>(dH, aj + 2, bi + LO + 2, idesc);
+                        mma_lo<KIND, 1, true>(dH, aj + LO + 2, bi + 2, idesc);
                         if (++stage == MP_STAGES) { stage = 0; phase ^= 1u; }
                     }
                     if (!ok) break;
@@ -197,14 +200,13 @@ __global__ void __launch_bounds__(MP_THREADS, 1) mp2_tc_kernel(const __grid_cons
                     // completed) right after its last product is issued
                     int sj = st0;
                     for (int cb = 0; cb < nb; cb++) {
-                        const uint32_t s = sbase + sj * MP_STAGE;
-                        for (int kk = 0; kk < 2; kk++) {
-                            const uint32_t off = kk * 32;
-                            tc_mma<KIND>(dG, sdesc(s + P_AI_HI * MP_TILE + off), sdesc(s + P_BJ_HI * MP_TILE + off),
-                                         idesc, 1u);
-                            tc_mma<KIND>(dH, sdesc(s + P_AJ_HI * MP_TILE + off), sdesc(s + P_BI_HI * MP_TILE + off),
-                                         idesc, 1u);
-                        }
+                        const uint32_t s = desc_lo(sbase + sj * MP_STAGE);
+                        const uint32_t ai = s + P_AI_HI * (MP_TILE >> 4), bj = s + P_BJ_HI * (MP_TILE >> 4);
+                        const uint32_t aj = s + P_AJ_HI * (MP_TILE >> 4), bi = s + P_BI_HI * (MP_TILE >> 4);
+                        mma_lo<KIND, 1, true>(dG, ai, bj, idesc);
+                        mma_lo<KIND, 1, true>(dH, aj, bi, idesc);
+                        mma_lo<KIND, 1, true>(dG, ai + 2, bj + 2, idesc);
+                        mma_lo<KIND, 1, true>(dH, aj + 2, bi + 2, idesc);
                         tc_commit(smem_u32(&bar_empty[sj]));
                         if (++sj == MP_STAGES) sj = 0;
                     }
