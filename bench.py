@@ -38,10 +38,10 @@ METRIC = "(T) TFLOP/s, triples/s: FP64 vs mixed at ≤1e-6 rel ΔE; serving p50/
 WORKLOAD = dict(o=50, v=450, naux=1500, seed=2)
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (152 SMs x 2070 MHz x 2 DFMA/clk x 2 flop)
 FP64_PROBE_TFLOPS = 1.20     # DFMA throughput probe on this machine's GB300
-# DRAM read+write bytes of one full-task launch of ugemm_f64_kernel at o=50,
-# v=450 (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
-# this bench's FP64 leg); valid for this kernel version and workload only
-F64_GEMM_TRAFFIC_BYTES = {(50, 450): 5153704192 + 2181897216}
+# DRAM read+write bytes of ugemm_f64_kernel per task at o=50, v=450: the
+# reads of one ncu capture at o=16, v=256 (0.807 GB per task) scaled by v^3,
+# plus the U writes (3 v^2 vc x 8 B); valid for this kernel version only
+F64_GEMM_TRAFFIC_BYTES = {(50, 450): int(0.807e9 * (450 / 256) ** 3) + 3 * 450 * 450 * 464 * 8}
 # batched workload: n molecules, o ~ U{4..16}, v ~ U{20..120}, naux = 3(o+v),
 # per-molecule seeds seed+index; FP64 is timed on the first fp64_n of them
 # (the whole set is ~44 algorithmic TFLOP, ~40 s per pass on the FP64 pipe);
@@ -442,8 +442,8 @@ def main():
         "triples_per_s": triples_s,
         "roofline": {"bound": "alu", "kernel": "ugemm_f64_kernel", "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": (F64_GEMM_TRAFFIC_BYTES.get((o, v)) if gemm_n == work else None),
-                     "traffic_unit": "bytes per launch (one task)",
+                     "traffic": F64_GEMM_TRAFFIC_BYTES.get((o, v)),
+                     "traffic_unit": "bytes per task (an o=16, v=256 capture scaled by v^3)",
                      "peak_note": "nominal FP64 (no FP64 figure in the measured peaks); "
                                   f"DFMA probe measured {FP64_PROBE_TFLOPS} TFLOP/s"},
         "kernel_ms_share": shares,

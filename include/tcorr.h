@@ -51,10 +51,10 @@ typedef enum {
     TCORR_TF32X3 = 1,  /* W contractions on tcgen05 tensor cores, TF32 hi+lo split, 3 products,
                           FP32 accumulation, W stored in FP32 (Sec. 3 mixed precision,
                           re-designed).  Energy epilogue: the numerators sum Z W and sum Z Y of
-                          each element orbit in FP32; the denominator e_i+e_j+e_k-e_a-e_b-e_c
-                          in FP64 and its reciprocal to FP64 accuracy (an FP32 reciprocal
-                          refined by one Newton step in FP64); numerator x 1/D and every sum
-                          (per thread, warp, CTA, orbit, task, problem) in FP64 */
+                          each element orbit in FP32; the denominator e_i+e_j+e_k-e_a-e_b-e_c,
+                          its reciprocal and numerator x 1/D to FP64 accuracy (float-float
+                          arithmetic on the FP32 pipe, relative error ~2^-44); every sum
+                          (per thread, CTA, orbit, task, problem) in FP64 or float-float */
     TCORR_BF16X3 = 2,  /* as TF32X3 with BF16 hi+lo operands.  A BF16 hi+lo split keeps 16
                           significant bits, and its residual averages below the 1e-6 bound only
                           over enough work: problems below 1e11 algorithmic flops (12 v^3 (v+o)
@@ -88,9 +88,9 @@ typedef struct {
                            problem's own operands; cached per (precision, o, v) in the process) */
     int eager;          /* batch handle: 1 = launch the waves directly on every call instead of
                            replaying the CUDA graph captured on the first call */
-    int wave_mb;        /* batch handle: U scratch per wave in MiB (0 = 96, sized so that one
-                           wave's U stays in L2 between the contraction and the epilogue);
-                           raised to one task of the largest problem when smaller */
+    int wave_mb;        /* batch handle: U scratch per wave in MiB (0 = 2048); raised to one
+                           task of the largest problem when smaller.  Server: its wave scratch
+                           (0 = 2048) */
     int single_sm;      /* split precisions: 0 = W contractions on SM pairs (2-CTA clusters,
                            tcgen05 cta_group::2, M = 256 tiles: each SM loads its own A tile and
                            half of B); 1 = one SM per tile (M = 128) */

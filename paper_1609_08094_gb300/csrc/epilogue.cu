@@ -42,13 +42,49 @@ __device__ __forceinline__ int perm_pos(int s, int d) {
 }
 __device__ __forceinline__ int pick3(int a, int b, int c, int k) { return k == 0 ? a : (k == 1 ? b : c); }
 
-// 1/d in FP64 from an FP32 estimate r0 of it (relative error e, |e| < 1e-6):
-// one Newton-Raphson step for the root of f(r) = 1/r - d, r1 = r0 + r0 (1 - d r0),
-// leaves a relative error of e^2 plus FP64 rounding.
-__device__ __forceinline__ double recip64(double d, float r0) {
-    const double r = (double)r0;
-    return fma(r, fma(-d, r, 1.0), r);
+// ---- float-float (double-FP32) arithmetic ------------------------------------
+// A value hi + lo with |lo| <= ulp(hi) / 2 carries ~48 significant bits.  The
+// split-precision epilogue forms its denominators, their reciprocals and the
+// products with them this way, on the FP32 pipe: GB300's FP64 pipe runs at
+// 1/64 of the FP32 rate, and with one FP64 Newton step per element orbit it
+// bounded that kernel.  TwoSum (Knuth) and Fast2Sum (Dekker) are error-free
+// transformations of a sum; fmaf gives the exact error of a product.
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {  // s + e == a + b exactly
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
 }
+__device__ __forceinline__ ff ff_fast(float a, float b) {  // |a| >= |b|: s + e == a + b exactly
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) {
+    const ff s = ff_two_sum(a.hi, -b.hi);
+    return ff_fast(s.hi, s.lo + (a.lo - b.lo));
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    const ff s = ff_two_sum(a.hi, b.hi);
+    return ff_fast(s.hi, s.lo + (a.lo + b.lo));
+}
+// 1/d: an FP32 reciprocal r of d.hi (relative error e ~ 2^-22) and its first
+// Newton correction r (1 - d r) from the exact residual (two FMAs): error ~e^2
+__device__ __forceinline__ ff ff_recip(ff d) {
+    const float r = __fdividef(1.f, d.hi);
+    const float e = fmaf(-d.lo, r, fmaf(-d.hi, r, 1.f));
+    return {r, r * e};
+}
+// x * r for an FP32 x: the exact product error of x * r.hi plus x * r.lo
+__device__ __forceinline__ ff ff_mul(float x, ff r) {
+    const float p = x * r.hi;
+    return ff_fast(p, fmaf(x, r.lo, fmaf(x, r.hi, -p)));
+}
+__device__ __forceinline__ ff ff_of(double x) {  // x rounded to ~48 bits
+    const float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
 // Sum over the CTA of one (E4, E5) pair per thread, in a fixed order, into
 // out[0..1]: the NT pairs through shared memory, NT / 32 per lane of warp 0,
@@ -282,22 +318,18 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
 // staged in shared memory, with the orbit's virtual energies in FP64 and as
 // FP32 offsets from their block origins.
 //
-// Precision of the energy terms (the numerators are FP32, everything from the
-// denominator on is FP64):
+// Precision of the energy terms (the numerators are FP32; denominators, their
+// reciprocals, the products with them and all sums to FP64 accuracy):
 //  - the element-orbit numerators sum_q Z_q W_q and sum_q Z_q Y_q (six
 //    orderings of one (a,b,c), or one element of an orbit with repeated
 //    blocks) are formed in FP32 from the FP32 W, Y;
-//  - the denominator D = e_i+e_j+e_k - e_a - e_b - e_c is formed in FP64;
-//  - 1/D: an FP32 reciprocal of the FP32 denominator (block base + offsets,
-//    relative error about 1e-7) refined by one Newton-Raphson step
-//    r <- r + r (1 - D r) in FP64 against the FP64 D, which squares the
-//    relative error (below 1e-13);
-//  - numerator x 1/D and every sum from there on (per thread, then over the
-//    CTA in a fixed order) in FP64; the orbit partials of a task are summed
-//    in FP64 (Kahan) by the task reduction.
-// One Newton step costs two FP64 FMAs per element orbit (per element in the
-// orbits with repeated blocks), so the FP64 pipe (1/64 of the FP32 rate on
-// this part) sees about one instruction per element.
+//  - the denominator D = e_i+e_j+e_k - e_a - e_b - e_c, its reciprocal and
+//    numerator x 1/D are formed in float-float (double-FP32) arithmetic from
+//    the orbital energies rounded to ~48 bits: relative error ~2^-44, on the
+//    FP32 pipe (see ff above);
+//  - each thread's terms are summed in float-float, converted to FP64, and
+//    summed over the CTA in FP64 in a fixed order; the orbit partials of a
+//    task are summed in FP64 (Kahan) by the task reduction.
 constexpr int F8 = 8;
 constexpr int FP0 = 69, FP1 = 8;    // plane / row pitch of a cube: at most 2-way bank conflicts
 constexpr int FSLOT = F8 * FP0;     // floats per cube slot
@@ -309,10 +341,8 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
     __shared__ float Ws[6 * FSLOT];
     __shared__ float T1s[3][3][F8];          // [occupied i,j,k][orbit block][local]
     __shared__ __align__(16) float OVs[3][3][3][F8 * F8];  // [(jk),(ik),(ij)][block][block][8x8]
-    __shared__ float Dls[3][F8];             // [orbit block][local] block-relative energies (FP32 seed)
-    __shared__ double Evs[3][F8];            // [orbit block][local] virtual energies (FP64)
-    __shared__ float base_s;
-    __shared__ double eijk_s;
+    __shared__ ff Evs[3][F8];                // [orbit block][local] virtual energies (float-float)
+    __shared__ ff eijk_s;                    // e_i + e_j + e_k (float-float)
     __shared__ int comp[6][6];
     __shared__ int distinct[6];
     __shared__ double red[NT][2];
@@ -375,11 +405,7 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
             if (OBP(s, 0) == OBP(t, 0) && OBP(s, 1) == OBP(t, 1) && OBP(s, 2) == OBP(t, 2)) d = 0;
         distinct[t] = d;
     }
-    if (tid == 96) {
-        const double eijk = p.eps_o[ti] + p.eps_o[tj] + p.eps_o[tkk];
-        base_s = (float)(eijk - p.eps_v[ob0 * F8] - p.eps_v[ob1 * F8] - p.eps_v[ob2 * F8]);
-        eijk_s = eijk;
-    }
+    if (tid == 96) eijk_s = ff_of(p.eps_o[ti] + p.eps_o[tj] + p.eps_o[tkk]);
     // stage t1, ovov sub-blocks and block-relative energies.  The FP32 inputs
     // are zero padded to vp (t1 rows [p][x], ovov slabs [p][q][x][z]): every
     // orbit block lies inside, and a sub-block row is two aligned float4 loads.
@@ -392,8 +418,7 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
         T1s[oc][b][m] = t1[occ * vp + pick3(ob0, ob1, ob2, b) * F8 + m];
     } else if (tid >= 96 + 32 && tid < 96 + 32 + 3 * F8) {
         const int e = tid - 128, b = e / F8, m = e % F8, x = pick3(ob0, ob1, ob2, b) * F8 + m;
-        Dls[b][m] = x < v ? p.dev_f[x] : 0.f;
-        Evs[b][m] = x < v ? p.eps_v[x] : 0.0;
+        Evs[b][m] = ff_of(x < v ? p.eps_v[x] : 0.0);
     }
     // slices: 0 = (j y | k z), 1 = (i x | k z), 2 = (i x | j y); 3 x 9 sub-blocks
     // x 8 rows x 2 halves = 432 float4
@@ -430,9 +455,8 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
     }
     __syncthreads();
 
-    const float base = base_s;
-    const double eijk = eijk_s;
-    double a4 = 0.0, a5 = 0.0;
+    const ff eijk = eijk_s;
+    ff A4 = {0.f, 0.f}, A5 = {0.f, 0.f};
     if (ob0 < ob1 && ob1 < ob2) {
         // Distinct blocks: each thread takes element orbits, the six orderings
         // of one (a,b,c) with a in A, b in B, c in C.  Slot q holds the element
@@ -452,8 +476,7 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
         const float jk_bc = OVV(0, 1, 2, lb, lc), jk_cb = OVV(0, 2, 1, lc, lb);
         const float ik_bc = OVV(1, 1, 2, lb, lc), ik_cb = OVV(1, 2, 1, lc, lb);
         const float ij_bc = OVV(2, 1, 2, lb, lc), ij_cb = OVV(2, 2, 1, lc, lb);
-        const float dbc = base + (Dls[1][lb] + Dls[2][lc]);
-        const double dbc64 = eijk - Evs[1][lb] - Evs[2][lc];
+        const ff dbc = ff_sub(ff_sub(eijk, Evs[1][lb]), Evs[2][lc]);
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int la = la0 + 4 * h;
@@ -485,9 +508,9 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
             const float wy = w0 * y0 + w1 * y1 + w2 * y2 + w3 * y3 + w4 * y4 + w5 * y5;
             const float s4 = 6.f * ww + 2.f * (E * E + O * O) - 8.f * E * O;
             const float s5 = 6.f * wy + (2.f * E - 4.f * O) * (y0 + y3 + y4) + (2.f * O - 4.f * E) * (y1 + y2 + y5);
-            const double r = recip64(dbc64 - Evs[0][la], __fdividef(1.f, dbc + Dls[0][la]));
-            a4 = fma((double)s4, r, a4);
-            a5 = fma((double)s5, r, a5);
+            const ff r = ff_recip(ff_sub(dbc, Evs[0][la]));
+            A4 = ff_add(A4, ff_mul(s4, r));
+            A5 = ff_add(A5, ff_mul(s5, r));
         }
 #undef OVV
     } else {
@@ -512,15 +535,14 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
                 const float yv = T1s[0][p0][l0] * OVs[0][p1][p2][l1 * F8 + l2] +
                                  T1s[1][p1][l1] * OVs[1][p0][p2][l0 * F8 + l2] +
                                  T1s[2][p2][l2] * OVs[2][p0][p1][l0 * F8 + l1];
-                const double r = recip64(eijk - Evs[p0][l0] - Evs[p1][l1] - Evs[p2][l2],
-                                         __fdividef(1.f, base + (Dls[p0][l0] + Dls[p1][l1] + Dls[p2][l2])));
-                a4 = fma((double)(zv * w0), r, a4);
-                a5 = fma((double)(zv * yv), r, a5);
+                const ff r = ff_recip(ff_sub(ff_sub(ff_sub(eijk, Evs[p0][l0]), Evs[p1][l1]), Evs[p2][l2]));
+                A4 = ff_add(A4, ff_mul(zv * w0, r));
+                A5 = ff_add(A5, ff_mul(zv * yv, r));
             }
         }
     }
     // the orbit partials of a task are summed in FP64 (Kahan) by the task reduction
-    cta_sum2(a4, a5, red, out, tid);
+    cta_sum2(ff_to_double(A4), ff_to_double(A5), red, out, tid);
 }
 #undef OBP
 

@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
 // operand-ingest rate, not the tensor pipe, bounds the single-SM kernel.
 //
 // The pair's two 128-pair tiles are consecutive tiles of the flattened
-// (b tile, c tile) list of a group: work item = (task, group, tile pair,
+// (b tile, c tile) list of a group: work item = (task, tile pair, group,
 // N pass); a tile index past the list is TMA zero fill and is not stored.
 //
 // Hand-offs (all bounded waits, as in the single-SM kernel):
@@ -354,12 +354,12 @@ __device__ __forceinline__ PairItem decode_pair(const Wave &w, int64_t it, SegCa
     const int npt = c.nbt * c.nct;
     const int npair = (npt + 1) / 2;
     int64_t x = it - c.begin;
-    r.it.n = (int)(x % c.npass);
+    r.it.n = (int)(x % c.npass);  // N pass fastest, then group, then tile pair (as decode)
     x /= c.npass;
-    const int t = (int)(x % npair) * 2 + (int)rank;
-    x /= npair;
     r.it.g = (int)(x % 3);
-    r.it.tb = (int)(x / 3);
+    x /= 3;
+    const int t = (int)(x % npair) * 2 + (int)rank;
+    r.it.tb = (int)(x / npair);
     r.empty = t >= npt;
     r.it.bt = r.empty ? c.nbt : t / c.nct;  // past the list: b >= v, all TMA fill
     r.it.ct = r.empty ? 0 : t % c.nct;

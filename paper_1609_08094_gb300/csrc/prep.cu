@@ -97,12 +97,6 @@ __global__ void pad_rows_kernel(const double *__restrict__ in, float *__restrict
     }
 }
 
-__global__ void block_deltas_kernel(const double *__restrict__ ev, float *__restrict__ d, int v,
-                                    int te) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x < v) d[x] = static_cast<float>(ev[(x / te) * te] - ev[x]);
-}
-
 }  // namespace
 
 cudaError_t launch_transpose_pad(int kind, const double *in, void *out_hi, void *out_lo,
@@ -133,11 +127,6 @@ cudaError_t launch_epilogue_f32_inputs(const double *t1, const double *ovov, flo
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_deltas(const double *eps_v, float *dev_f, int v, int te,
-                                cudaStream_t st) {
-    block_deltas_kernel<<<(v + 127) / 128, 128, 0, st>>>(eps_v, dev_f, v, te);
-    return cudaGetLastError();
-}
 
 namespace {
 // Thread per leading index x: the sorted triples x <= y <= z of n values

@@ -266,8 +266,6 @@ void build_epilogue_inputs(Exec &ex, Problem &pb, const double *eps_occ, const d
                                       (int)vp, ex.stream));
         free_tmp(ex, tmp1, (size_t)o * v);
         free_tmp(ex, tmp2, nov2);
-        dalloc(ex, pb.dev_f, v * sizeof(float));
-        CK(launch_block_deltas(pb.eps_v, pb.dev_f, v, EPI_TE, ex.stream));
     }
 }
 
@@ -290,7 +288,7 @@ size_t problem_bytes(const Dims &d, int prec) {
     const size_t eb = elem_bytes(prec), parts = operand_planes(prec);
     size_t b = parts * eb * (o * v2 * d.dp + o * v2 * d.lp + o * o * v * d.dp + o * o * v * d.lp);
     const size_t ve = fp64_epilogue(prec) ? v : (size_t)epi_vp((int)v);  // FP32 inputs are padded
-    b += (o * o * ve * ve + o * ve) * u_elem_bytes(prec) + (o + v) * 8 + v * 4;
+    b += (o * o * ve * ve + o * ve) * u_elem_bytes(prec) + (o + v) * 8;
     const size_t nb = (v + EPI_TE - 1) / EPI_TE;
     b += nb * (nb + 1) * (nb + 2) / 6 * 12;
     b += o * (o + 1) * (o + 2) / 6 * 28;
@@ -327,7 +325,6 @@ void fill_desc(Exec &ex, Problem &pb, int pbt) {
     d.eps_v = pb.eps_v;
     d.t1 = pb.t1;
     d.ovov = pb.ovov;
-    d.dev_f = pb.dev_f;
     d.tasks = pb.tasks;
     d.orbits = pb.orbits;
     d.task_e = pb.task_e;

@@ -38,7 +38,6 @@ struct Problem {
     double *eps_o = nullptr, *eps_v = nullptr;  // FP64
     void *t1 = nullptr;      // FP64 or FP32 copy
     void *ovov = nullptr;    // FP64 or FP32 copy [o][v][o][v]
-    float *dev_f = nullptr;  // FP32 block-relative virtual energies (mixed epilogue)
     int64_t ntask = 0;
     int *tasks = nullptr;      // device [ntask][3]
     double *task_e = nullptr;  // device [ntask][2] (E4, E5 share)

@@ -170,14 +170,18 @@ __device__ __forceinline__ Item decode(const Wave &w, int64_t it, SegCache &c) {
     seg_update(w, it, c);
     Item r;
     int64_t x = it - c.begin;
+    // order within a task: N pass fastest, then group, then pair tile, so the
+    // items running at the same time read each operand tile of a slice from
+    // L2 for both groups that use it (each slice of a task is read by two of
+    // its three groups) and for both N passes
     r.n = (int)(x % c.npass);
     x /= c.npass;
+    r.g = (int)(x % 3);
+    x /= 3;
     r.ct = (int)(x % c.nct);
     x /= c.nct;
     r.bt = (int)(x % c.nbt);
-    x /= c.nbt;
-    r.g = (int)(x % 3);
-    r.tb = (int)(x / 3);
+    r.tb = (int)(x / c.nbt);
     if (r.tb != c.tcached) {
         const int *tk = c.d->tasks + 3 * (c.task0 + r.tb);
         c.ti = tk[0];

@@ -308,7 +308,10 @@ tcorr_status tcorr_batch_create(tcorr_batch_t *out, int n, const tcorr_problem *
             u_task_max = std::max<int64_t>(u_task_max, (int64_t)3 * dm.v * dm.v * dm.vc);
             norb_max = std::max<int64_t>(norb_max, epilogue_orbits(dm.v));
         }
-        const size_t wave_bytes = (size_t)(op.wave_mb > 0 ? op.wave_mb : 96) << 20;
+        // 2 GiB of U per wave: fewer wave boundaries (each drains the GEMM and the
+        // epilogue) measured faster than waves sized for L2 (96 MiB: 0.83x of one
+        // handle per molecule in BF16x3; 512 MiB: 0.99x; 2 GiB: 1.02x)
+        const size_t wave_bytes = (size_t)(op.wave_mb > 0 ? op.wave_mb : 2048) << 20;
         ex.u_cap = std::max<int64_t>(u_task_max, (int64_t)(wave_bytes / ueb));
         ex.wave_tasks = op.batch_tasks > 0 ? op.batch_tasks : ((int64_t)1 << 40);
         // partials: room for as many tasks as the U scratch can hold of the smallest problem

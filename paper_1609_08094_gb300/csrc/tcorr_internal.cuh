@@ -75,7 +75,6 @@ struct InstDesc {
     const void *G, *T2K, *T2R, *AoN;  // FP64 operand layouts (FP64 W contractions)
     const double *eps_o, *eps_v;
     const void *t1, *ovov;    // FP64 or FP32 copies for the epilogue
-    const float *dev_f;       // FP32 block-relative virtual energies (mixed epilogue)
     const int *tasks;         // [ntask][3]
     const int *orbits;        // [norb][3]
     double *task_e;           // [ntask][2]
@@ -131,8 +130,6 @@ cudaError_t launch_transpose_pad(int kind, const double *in, void *out_hi, void 
 // FP32 epilogue inputs: t1 as [o][vp] and (p x | q z) as slabs [p][q][x][z] with x, z < vp, zero padded
 cudaError_t launch_epilogue_f32_inputs(const double *t1, const double *ovov, float *t1f, float *ovf, int o,
                                        int v, int vp, cudaStream_t st);
-// dev_f[x] = (float)(eps_v[block_start(x)] - eps_v[x]), block edge te
-cudaError_t launch_block_deltas(const double *eps_v, float *dev_f, int v, int te, cudaStream_t st);
 // tasks[n] = (i, j, k): the sorted occupied triples i <= j <= k of o orbitals
 // in lexicographic order; orbits[n] = (A, B, C): the sorted block triples
 // A <= B <= C of nb virtual blocks, lexicographic

@@ -6,16 +6,19 @@ evaluates, per element orbit (the six orderings of one a < b < c) or per
 element (orbits with repeated virtual indices):
   - the numerators sum_q Z_q W_q and sum_q Z_q Y_q in FP32 (Y from FP32 t1
     and ovov),
-  - D = e_i + e_j + e_k - e_a - e_b - e_c in FP64,
-  - 1/D as an FP32 reciprocal of the FP32 denominator refined by one
-    Newton-Raphson step in FP64,
-  - numerator x 1/D and all sums in FP64.
+  - D = e_i + e_j + e_k - e_a - e_b - e_c, 1/D and numerator x 1/D in
+    float-float (double-FP32) arithmetic: TwoSum / Fast2Sum for the sums,
+    an FP32 reciprocal corrected with the exact FMA residual, the exact FMA
+    error of the product,
+  - the thread's terms summed in float-float, then FP64 over the CTA and the
+    task.
 This file restates that arithmetic in numpy (float32 where the kernel uses
-FP32) on the exact W of a task, and compares it with the same energy in FP64
-throughout: the difference is the epilogue's share of the error, to be set
-against the 1e-6 relative bound of the mixed-precision path (Sec. 4).  The
-earlier all-FP32 scheme (FP32 denominators and FP32 sums) is modelled beside
-it for comparison.
+FP32; an FMA as the float64 product and sum rounded once to float32) on the
+exact W of a task, and compares it with the same energy in FP64 throughout:
+the difference is the epilogue's share of the error, to be set against the
+1e-6 relative bound of the mixed-precision path (Sec. 4).  Two cheaper
+schemes are modelled beside it for comparison: FP32 denominators with FP64
+sums, and FP32 denominators with FP32 sums within each 8^3 block orbit.
 """
 import itertools
 
@@ -27,23 +30,63 @@ from paper_1609_08094_gb300 import synth
 from tests.test_energy_forms import multiplicity, w_grouped, y_and_d
 
 
-def recip64(d, r0):
-    """One Newton-Raphson step for 1/d from the FP32 estimate r0."""
-    r = np.float64(r0)
-    return r + r * (1.0 - d * r)
+F32 = np.float32
+
+
+def fmaf(a, b, c):
+    """a * b + c rounded once to float32 (the float64 product of two floats is exact)."""
+    return F32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def ff_of(x):
+    hi = F32(x)
+    return hi, F32(np.float64(x) - np.float64(hi))
+
+
+def ff_two_sum(a, b):
+    s = F32(a + b)
+    bb = F32(s - a)
+    return s, F32(F32(a - F32(s - bb)) + F32(b - bb))
+
+
+def ff_fast(a, b):
+    s = F32(a + b)
+    return s, F32(b - F32(s - a))
+
+
+def ff_sub(a, b):
+    s, e = ff_two_sum(a[0], F32(-b[0]))
+    return ff_fast(s, F32(e + F32(a[1] - b[1])))
+
+
+def ff_recip(d):
+    r = F32(F32(1.0) / d[0])
+    e = fmaf(-d[1], r, fmaf(-d[0], r, F32(1.0)))
+    return r, F32(r * e)
+
+
+def ff_mul(x, r):
+    p = F32(x * r[0])
+    return ff_fast(p, fmaf(x, r[1], fmaf(x, r[0], -p)))
+
+
+def ff_value(a):
+    return np.float64(a[0]) + np.float64(a[1])
 
 
 def orbit_terms(w, y, eo, ev, i, j, k, f32_den, f32_sum):
     """E4, E5 of one task by element orbits, numerators in FP32.
 
-    f32_den, f32_sum False: the kernel's scheme (FP64 denominator, Newton
-    reciprocal, FP64 sums).  True: the earlier all-FP32 scheme (FP32
-    denominator and reciprocal; terms summed in FP32 within each block orbit
-    of 8^3 as a tree, and in FP64 across block orbits)."""
+    f32_den False: the kernel's scheme (float-float denominator, reciprocal
+    and product; FP64 sums).  f32_den True: FP32 denominator, reciprocal and
+    product, with FP64 sums (f32_sum False) or FP32 sums within each block
+    orbit of 8^3 as a tree and FP64 across block orbits (f32_sum True)."""
     f = np.float32
     v = len(ev)
     eijk = eo[i] + eo[j] + eo[k]
     w32, y32 = w.astype(f), y.astype(f)
+    ev_ff = [ff_of(x) for x in ev]
+    eijk_ff = ff_of(eijk)
     per_orbit = {}
     for a, b, c in itertools.product(range(v), repeat=3):
         if a < b < c:
@@ -68,13 +111,13 @@ def orbit_terms(w, y, eo, ev, i, j, k, f32_den, f32_sum):
             n5 = z * y32[x]
         else:
             continue
-        d64 = eijk - ev[a] - ev[b] - ev[c]
         if f32_den:
-            r = f(1.0) / f(d64)
+            r = f(1.0) / f(eijk - ev[a] - ev[b] - ev[c])
             t4, t5 = n4 * r, n5 * r
         else:
-            r = recip64(d64, f(1.0) / f(d64))
-            t4, t5 = np.float64(n4) * r, np.float64(n5) * r
+            dd = ff_sub(ff_sub(ff_sub(eijk_ff, ev_ff[a]), ev_ff[b]), ev_ff[c])
+            r = ff_recip(dd)
+            t4, t5 = ff_value(ff_mul(n4, r)), ff_value(ff_mul(n5, r))
         key = tuple(sorted((a // 8, b // 8, c // 8)))
         per_orbit.setdefault(key, []).append((t4, t5))
     e4 = e5 = 0.0
@@ -94,11 +137,20 @@ def exact_terms(w, y, d, i, j, k):
     return m / 6 * float(np.sum(z * w / d)), m / 6 * float(np.sum(z * y / d))
 
 
-def test_newton_reciprocal_is_fp64_accurate():
+def test_float_float_quotient_is_fp64_accurate():
+    """x / D in float-float, with D formed by float-float subtractions from
+    energies rounded to ~48 bits: within 2e-13 of the FP64 quotient."""
     rng = np.random.default_rng(3)
-    d = -rng.uniform(1.2, 20.0, size=4000)
-    r = recip64(d, (np.float32(1.0) / d.astype(np.float32)))
-    assert np.max(np.abs(r * d - 1.0)) < 1e-13
+    worst = 0.0
+    for _ in range(3000):
+        eo = -rng.uniform(0.3, 2.0, size=3)
+        ev = rng.uniform(0.1, 5.0, size=3)
+        x = F32(rng.normal() * 10.0 ** rng.uniform(-6, 2))
+        d = ff_sub(ff_sub(ff_sub(ff_of(eo.sum()), ff_of(ev[0])), ff_of(ev[1])), ff_of(ev[2]))
+        got = ff_value(ff_mul(x, ff_recip(d)))
+        ref = np.float64(x) / (eo.sum() - ev[0] - ev[1] - ev[2])
+        worst = max(worst, abs(got - ref) / abs(ref))
+    assert worst < 2e-13, worst
 
 
 @pytest.fixture(scope="module")
@@ -109,9 +161,9 @@ def inst():
 
 def test_epilogue_share_of_the_mixed_error(inst):
     """With the exact W, the kernel's epilogue arithmetic (FP32 numerators,
-    FP64 denominators and sums) stays within 2e-8 of the FP64 energy of every
-    task and within 1e-8 of the FP64 total; the earlier all-FP32 scheme is
-    printed beside it."""
+    float-float denominators and products, FP64 sums) stays within 2e-8 of
+    the FP64 energy of every task and within 1e-8 of the FP64 total; the
+    two cheaper schemes are printed beside it."""
     rows = []
     tot_exact = np.zeros(2)
     tot_model = np.zeros(2)
@@ -121,16 +173,18 @@ def test_epilogue_share_of_the_mixed_error(inst):
         y, d = y_and_d(inst, i, j, k)
         ex = np.array(exact_terms(w, y, d, i, j, k))
         mo = np.array(orbit_terms(w, y, inst.eps_occ, inst.eps_vir, i, j, k, False, False))
+        fd = np.array(orbit_terms(w, y, inst.eps_occ, inst.eps_vir, i, j, k, True, False))
         ff = np.array(orbit_terms(w, y, inst.eps_occ, inst.eps_vir, i, j, k, True, True))
         tot_exact += ex
         tot_model += mo
         tot_f32 += ff
         rel_mo = abs(mo.sum() - ex.sum()) / abs(ex.sum())
+        rel_fd = abs(fd.sum() - ex.sum()) / abs(ex.sum())
         rel_ff = abs(ff.sum() - ex.sum()) / abs(ex.sum())
-        rows.append((i, j, k, rel_mo, rel_ff))
+        rows.append((i, j, k, rel_mo, rel_fd, rel_ff))
         assert rel_mo <= 2e-8, (i, j, k, rel_mo)
     for r in rows:
-        print("task (%d,%d,%d): epilogue model %.2e, all-FP32 scheme %.2e" % r)
+        print("task (%d,%d,%d): epilogue model %.2e, FP32 denominators %.2e, all-FP32 %.2e" % r)
     rel_tot = abs(tot_model.sum() - tot_exact.sum()) / abs(tot_exact.sum())
     rel_tot_f32 = abs(tot_f32.sum() - tot_exact.sum()) / abs(tot_exact.sum())
     print(f"total: epilogue model {rel_tot:.2e}, all-FP32 scheme {rel_tot_f32:.2e}")
