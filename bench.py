@@ -42,6 +42,13 @@ FP64_PROBE_TFLOPS = 1.20     # DFMA throughput probe on this machine's GB300
 # reads of one ncu capture at o=16, v=256 (0.807 GB per task) scaled by v^3,
 # plus the U writes (3 v^2 vc x 8 B); valid for this kernel version only
 F64_GEMM_TRAFFIC_BYTES = {(50, 450): int(0.807e9 * (450 / 256) ** 3) + 3 * 450 * 450 * 464 * 8}
+# the same for the tensor-core contractions (SM-pair kernel, FP64 emulation): reads
+# per task of one ncu capture at o=16, v=256 scaled by v^3, plus the U writes
+TC_GEMM_TRAFFIC_BYTES = {
+    ("bf16x3", 50, 450): int(0.2575e9 * (450 / 256) ** 3) + 3 * 450 * 450 * 464 * 4,
+    ("tf32x3", 50, 450): int(0.539e9 * (450 / 256) ** 3) + 3 * 450 * 450 * 464 * 4,
+    ("fp64_oz", 50, 450): int(0.503e9 * (450 / 256) ** 3) + 3 * 450 * 450 * 464 * 8,
+}
 # batched workload: n molecules, o ~ U{4..16}, v ~ U{20..120}, naux = 3(o+v),
 # per-molecule seeds seed+index; FP64 is timed on the first fp64_n of them
 # (the whole set is ~44 algorithmic TFLOP, ~40 s per pass on the FP64 pipe);
@@ -358,7 +365,9 @@ def main():
                 ent["roofline"] = {
                     "bound": "tensor", "kernel": "ugemm_oz_kernel (FP64 emulation, BF16 slices)",
                     "achieved": ent["gemm_tflops"], "peak": peak, "unit": "TFLOP/s",
-                    "frac": ent["gemm_tflops"] / peak, "traffic": None,
+                    "frac": ent["gemm_tflops"] / peak,
+                    "traffic": TC_GEMM_TRAFFIC_BYTES.get((prec, o, v)),
+                    "traffic_unit": "bytes per task (an o=16, v=256 capture scaled by v^3)",
                     "tensor_achieved": 15 * ent["gemm_tflops"],
                     "tensor_frac": 15 * ent["gemm_tflops"] / peak,
                     "fp64_pipe_peak": FP64_PEAK_TFLOPS,
@@ -368,9 +377,12 @@ def main():
                             "dense burst of " + pk["source"] + " peaks"}
             elif ent["gemm_tflops"]:
                 ent["roofline"] = {
-                    "bound": "tensor", "kernel": f"ugemm_tc_kernel ({prec})",
+                    "bound": "tensor",
+                    "kernel": f"{'ugemm_tc_kernel' if args.single_sm else 'ugemm_tc_pair_kernel'} ({prec})",
                     "achieved": ent["gemm_tflops"], "peak": peak, "unit": "TFLOP/s",
-                    "frac": ent["gemm_tflops"] / peak, "traffic": None,
+                    "frac": ent["gemm_tflops"] / peak,
+                    "traffic": None if args.single_sm else TC_GEMM_TRAFFIC_BYTES.get((prec, o, v)),
+                    "traffic_unit": "bytes per task (an o=16, v=256 capture scaled by v^3)",
                     "tensor_achieved": 3 * ent["gemm_tflops"],
                     "tensor_frac": 3 * ent["gemm_tflops"] / peak,
                     "note": ("achieved counts algorithmic flops (12 v^3 (v+o) per task); the "
@@ -601,12 +613,15 @@ def bench_batched(args, rank, world, stream):
         ms_solo = solo(prec, insts)
         out["precisions"][prec] = {
             "molecules": len(insts) * world, "value": fl / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
-            "triples_per_s": ntask(insts) * world / (ms * 1e-3), "ms_per_step": ms, "steps": args.steps,
+            "triples_per_s": ntask(insts) * world / (ms * 1e-3), "ms_per_step": ms, "steps": min(args.steps, 3),
             "warmup": min(args.warmup, 3), "waves": wv, "gpu_launches": nl, "tiles_pb": tiles,
             "kernel_ms_share": {k: round(m / max(1e-9, tot), 4) for k, (m, _) in kt.items()},
-            "roofline": {"bound": "tensor", "kernel": f"ugemm_tc_kernel ({prec})", "achieved": gemm_tf,
+            "roofline": {"bound": "tensor",
+                         "kernel": "ugemm_oz_kernel (FP64 emulation)" if prec == "fp64_oz" else f"ugemm_tc_pair_kernel ({prec})",
+                         "achieved": gemm_tf,
                          "peak": peak, "unit": "TFLOP/s", "frac": gemm_tf / peak, "traffic": None,
-                         "tensor_achieved": 3 * gemm_tf, "tensor_frac": 3 * gemm_tf / peak},
+                         "tensor_achieved": (15 if prec == "fp64_oz" else 3) * gemm_tf,
+                         "tensor_frac": (15 if prec == "fp64_oz" else 3) * gemm_tf / peak},
             "rel_err_vs_fp64": {"max": float(rel.max()), "median": float(np.median(rel)),
                                 "results": int(rel.size)}, "tol": 1e-6 if prec != "fp64_oz" else 1e-10,
             "unbatched_ms": ms_solo, "speedup_vs_unbatched": ms_solo / ms,

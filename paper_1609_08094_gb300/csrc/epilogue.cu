@@ -86,6 +86,32 @@ __device__ __forceinline__ ff ff_of(double x) {  // x rounded to ~48 bits
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
+// As cta_sum2 for float-float pairs: summed in float-float (FP32 pipe) and
+// converted to FP64 once, by thread 0.
+__device__ __forceinline__ void cta_sum2_ff(ff a4, ff a5, ff (*red)[2], double *out, int tid) {
+    red[tid][0] = a4;
+    red[tid][1] = a5;
+    __syncthreads();
+    if (tid < 32) {
+        ff b4 = red[tid][0], b5 = red[tid][1];
+#pragma unroll
+        for (int k = 1; k < NT / 32; k++) {
+            b4 = ff_add(b4, red[tid + 32 * k][0]);
+            b5 = ff_add(b5, red[tid + 32 * k][1]);
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const ff c4 = {__shfl_xor_sync(0xffffffffu, b4.hi, off), __shfl_xor_sync(0xffffffffu, b4.lo, off)};
+            const ff c5 = {__shfl_xor_sync(0xffffffffu, b5.hi, off), __shfl_xor_sync(0xffffffffu, b5.lo, off)};
+            b4 = ff_add(b4, c4);
+            b5 = ff_add(b5, c5);
+        }
+        if (tid == 0) {
+            out[0] = ff_to_double(b4);
+            out[1] = ff_to_double(b5);
+        }
+    }
+}
+
 // Sum over the CTA of one (E4, E5) pair per thread, in a fixed order, into
 // out[0..1]: the NT pairs through shared memory, NT / 32 per lane of warp 0,
 // then a shuffle tree.  (A shuffle tree over all NT threads would put ten
@@ -327,8 +353,8 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
 //    numerator x 1/D are formed in float-float (double-FP32) arithmetic from
 //    the orbital energies rounded to ~48 bits: relative error ~2^-44, on the
 //    FP32 pipe (see ff above);
-//  - each thread's terms are summed in float-float, converted to FP64, and
-//    summed over the CTA in FP64 in a fixed order; the orbit partials of a
+//  - the terms are summed in float-float per thread and over the CTA (a
+//    fixed order), converted to FP64 once per orbit; the orbit partials of a
 //    task are summed in FP64 (Kahan) by the task reduction.
 constexpr int F8 = 8;
 constexpr int FP0 = 69, FP1 = 8;    // plane / row pitch of a cube: at most 2-way bank conflicts
@@ -345,7 +371,7 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
     __shared__ ff eijk_s;                    // e_i + e_j + e_k (float-float)
     __shared__ int comp[6][6];
     __shared__ int distinct[6];
-    __shared__ double red[NT][2];
+    __shared__ ff red[NT][2];
 
     const int64_t item = blockIdx.x;
     const Seg sg = wv.segs[seg_find(wv.segs, wv.nseg, item, [](const Seg &x) { return x.epi0; })];
@@ -542,7 +568,7 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
         }
     }
     // the orbit partials of a task are summed in FP64 (Kahan) by the task reduction
-    cta_sum2(ff_to_double(A4), ff_to_double(A5), red, out, tid);
+    cta_sum2_ff(A4, A5, red, out, tid);
 }
 #undef OBP
 

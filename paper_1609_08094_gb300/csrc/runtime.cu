@@ -104,6 +104,49 @@ size_t u_elem_bytes(int prec) { return fp64_epilogue(prec) ? 8 : 4; }
 // operand planes per element: 1 (FP64), 2 (hi + lo), or the FP64-emulation slices
 static size_t operand_planes(int prec) { return prec == TCORR_FP64 ? 1 : (is_split(prec) ? 2 : (size_t)oz_slices()); }
 
+// Streams a host array of v rows of `row` doubles to the device in chunks of
+// up to 512 MB and calls consume(stage, d0, nr) for each, which enqueues the
+// chunk's kernels on ex.stream.  Two staging buffers and a copy stream of
+// its own: the copy of chunk n+1 overlaps the kernels of chunk n (the host
+// array should be pinned for the copies to run asynchronously).
+struct CopyPipe {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[5] = {};  // start, copied[2], used[2]
+    ~CopyPipe() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+template <typename F>
+static void stream_rows(Exec &ex, const double *host, size_t row, int v, F consume) {
+    size_t rows_per = (size_t)((512ull << 20) / (row * sizeof(double)));
+    if (rows_per < 1) rows_per = 1;
+    if (rows_per > (size_t)v) rows_per = v;
+    const int nbuf = rows_per < (size_t)v ? 2 : 1;
+    double *stage[2] = {nullptr, nullptr};
+    for (int b = 0; b < nbuf; b++) dalloc(ex, stage[b], rows_per * row * sizeof(double));
+    CopyPipe cp;
+    CK(cudaStreamCreateWithFlags(&cp.cs, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : cp.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventRecord(cp.ev[0], ex.stream));  // the buffers exist in ex.stream's order
+    CK(cudaStreamWaitEvent(cp.cs, cp.ev[0], 0));
+    int k = 0;
+    for (int d0 = 0; d0 < v; d0 += (int)rows_per, k++) {
+        const int nr = (int)((size_t)(v - d0) < rows_per ? (size_t)(v - d0) : rows_per);
+        const int b = k % nbuf;
+        if (k >= nbuf) CK(cudaStreamWaitEvent(cp.cs, cp.ev[3 + b], 0));  // chunk k - nbuf consumed
+        CK(cudaMemcpyAsync(stage[b], host + (size_t)d0 * row, nr * row * sizeof(double), cudaMemcpyHostToDevice,
+                           cp.cs));
+        CK(cudaEventRecord(cp.ev[1 + b], cp.cs));
+        CK(cudaStreamWaitEvent(ex.stream, cp.ev[1 + b], 0));
+        consume(stage[b], d0, nr);
+        CK(cudaEventRecord(cp.ev[3 + b], ex.stream));
+    }
+    for (int b = 0; b < nbuf; b++) free_tmp(ex, stage[b], rows_per * row);  // synchronises ex.stream
+    CK(cudaStreamSynchronize(cp.cs));
+}
+
 // FP64 emulation: the operands as oz_slices() BF16 slice planes under one
 // power-of-two scale per operand side (exponents computed on the device from
 // max |vvvo|, |t2|, |ooov|, so nothing here waits for the device).
@@ -144,20 +187,11 @@ static void build_operands_oz(Exec &ex, Problem &pb, const double *t2, const dou
         CK(launch_slice_pad(vvvo, op.G, v2, v, v, o, o, (int64_t)row, 1, dp, (int64_t)v2 * dp, (int64_t)nG, eA, 1.0,
                             ex.stream));
     } else {
-        size_t rows_per = (size_t)((512ull << 20) / (row * sizeof(double)));
-        if (rows_per < 1) rows_per = 1;
-        if (rows_per > (size_t)v) rows_per = v;
-        double *stage = nullptr;
-        dalloc(ex, stage, rows_per * row * sizeof(double));
-        for (int d0 = 0; d0 < v; d0 += (int)rows_per) {
-            const int nr = (int)((size_t)(v - d0) < rows_per ? (size_t)(v - d0) : rows_per);
-            CK(cudaMemcpyAsync(stage, vvvo + (size_t)d0 * row, nr * row * sizeof(double), cudaMemcpyHostToDevice,
-                               ex.stream));
+        stream_rows(ex, vvvo, row, v, [&](const double *stage, int d0, int nr) {
             char *g = static_cast<char *>(op.G) + (size_t)d0 * 2;
             CK(launch_slice_pad(stage, g, v2, nr, nr, o, o, (int64_t)row, 1, dp, (int64_t)v2 * dp, (int64_t)nG, eA,
                                 1.0, ex.stream));
-        }
-        free_tmp(ex, stage, rows_per * row);
+        });
     }
     // T2K[p][q][xy][l] = slices of t2[q][l][xy]; T2R[p][spa][d] = slices of t2[spa][d]
     CK(launch_slice_pad(dt2, op.T2K, o, o, lp, v2, (int64_t)o * v2, v2, 1, (int64_t)v2 * lp, lp, (int64_t)nT2K, eA,
@@ -208,21 +242,12 @@ void build_operands(Exec &ex, Problem &pb, const double *t2, const double *vvvo,
         CK(launch_transpose_pad(kind, vvvo, op.G, op.Glo, v2, v, v, o, o, (int64_t)row, 1, dp,
                                 (int64_t)v2 * dp, 1.0, ex.stream));
     } else {
-        size_t rows_per = (size_t)((512ull << 20) / (row * sizeof(double)));
-        if (rows_per < 1) rows_per = 1;
-        if (rows_per > (size_t)v) rows_per = v;
-        double *stage = nullptr;
-        dalloc(ex, stage, rows_per * row * sizeof(double));
-        for (int d0 = 0; d0 < v; d0 += (int)rows_per) {
-            const int nr = (int)((size_t)(v - d0) < rows_per ? (size_t)(v - d0) : rows_per);
-            CK(cudaMemcpyAsync(stage, vvvo + (size_t)d0 * row, nr * row * sizeof(double),
-                               cudaMemcpyHostToDevice, ex.stream));
+        stream_rows(ex, vvvo, row, v, [&](const double *stage, int d0, int nr) {
             char *ghi = static_cast<char *>(op.G) + (size_t)d0 * eb;
             char *glo = split ? static_cast<char *>(op.Glo) + (size_t)d0 * eb : nullptr;
             CK(launch_transpose_pad(kind, stage, ghi, glo, v2, nr, nr, o, o, (int64_t)row, 1, dp,
                                     (int64_t)v2 * dp, 1.0, ex.stream));
-        }
-        free_tmp(ex, stage, rows_per * row);
+        });
     }
     double *tmp_t2 = nullptr, *tmp_oo = nullptr;
     const double *dt2 = device_view(ex, t2, (size_t)o * o * v2, host, tmp_t2);
