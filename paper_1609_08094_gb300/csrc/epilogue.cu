@@ -18,8 +18,13 @@
 // reading each U row contiguously, then evaluates Z, Y, D and the two energy
 // sums for every element of the distinct cubes, and reduces them with warp
 // shuffles to one FP64 pair.  Every element (a,b,c) of the task lies in
-// exactly one distinct cube of exactly one orbit.
-#include "tcorr_internal.cuh"
+// exactly one distinct cube of exactly one orbit.  (The mixed-precision
+// kernel further down takes the same orbits in a persistent, pipelined form.)
+#include <algorithm>
+#include <cstddef>
+#include <mutex>
+
+#include "tc_common.cuh"
 
 namespace tcorr {
 namespace {
@@ -86,32 +91,6 @@ __device__ __forceinline__ ff ff_of(double x) {  // x rounded to ~48 bits
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
-// As cta_sum2 for float-float pairs: summed in float-float (FP32 pipe) and
-// converted to FP64 once, by thread 0.
-__device__ __forceinline__ void cta_sum2_ff(ff a4, ff a5, ff (*red)[2], double *out, int tid) {
-    red[tid][0] = a4;
-    red[tid][1] = a5;
-    __syncthreads();
-    if (tid < 32) {
-        ff b4 = red[tid][0], b5 = red[tid][1];
-#pragma unroll
-        for (int k = 1; k < NT / 32; k++) {
-            b4 = ff_add(b4, red[tid + 32 * k][0]);
-            b5 = ff_add(b5, red[tid + 32 * k][1]);
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-            const ff c4 = {__shfl_xor_sync(0xffffffffu, b4.hi, off), __shfl_xor_sync(0xffffffffu, b4.lo, off)};
-            const ff c5 = {__shfl_xor_sync(0xffffffffu, b5.hi, off), __shfl_xor_sync(0xffffffffu, b5.lo, off)};
-            b4 = ff_add(b4, c4);
-            b5 = ff_add(b5, c5);
-        }
-        if (tid == 0) {
-            out[0] = ff_to_double(b4);
-            out[1] = ff_to_double(b5);
-        }
-    }
-}
-
 // Sum over the CTA of one (E4, E5) pair per thread, in a fixed order, into
 // out[0..1]: the NT pairs through shared memory, NT / 32 per lane of warp 0,
 // then a shuffle tree.  (A shuffle tree over all NT threads would put ten
@@ -157,7 +136,6 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
     const Seg sg = wv.segs[seg_find(wv.segs, wv.nseg, item, [](const Seg &x) { return x.epi0; })];
     const InstDesc &p = wv.descs[sg.inst];
     const int o = p.dm.o, v = p.dm.v, vc = p.dm.vc;
-    const int64_t v2 = (int64_t)v * v;
     const int tb = (int)((item - sg.epi0) / p.norb), orb = (int)((item - sg.epi0) % p.norb);
     const int *tk = p.tasks + 3 * (sg.task0 + tb);
     const int ti = tk[0], tj = tk[1], tkk = tk[2];
@@ -171,9 +149,9 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
     // below are issued before any barrier
     const int ob0 = p.orbits[3 * orb], ob1 = p.orbits[3 * orb + 1], ob2 = p.orbits[3 * orb + 2];
 #define OBP(s, d) pick3(ob0, ob1, ob2, perm_pos((s), (d)))
-    const UT *U0 = static_cast<const UT *>(wv.U) + sg.u_off + (int64_t)(tb * 3 + 0) * v2 * vc;
-    const UT *U1 = U0 + v2 * vc;
-    const UT *U2 = U1 + v2 * vc;
+    const UT *U0 = static_cast<const UT *>(wv.U) + sg.u_off + (int64_t)(tb * 3 + 0) * p.dm.ug;
+    const UT *U1 = U0 + p.dm.ug;
+    const UT *U2 = U1 + p.dm.ug;
     static_assert(sizeof(UT) == 8 && TE == 8, "16-byte loads of 8-element FP64 rows");
     // pass A loads: W = U0[x][y][z] + U1[y][x][z] (z fastest, pairs of z); pass B
     // loads: U2[z][x][y] (y fastest, pairs of y).  A row never ends within a
@@ -335,14 +313,32 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
 
 #undef OBP
 
-// Mixed-precision epilogue: the same block-orbit algorithm with 8^3 cubes of
-// FP32 W (the tensor-core contractions' output), sized for occupancy (about
-// 20 KB of shared memory, 5 CTAs per SM).  The U loads of a thread are issued
-// first, right after the orbit's block indices are read, and consumed after
-// the Y operands have been staged, so their latency overlaps the staging.
-// The Y operands of the orbit (t1 rows and the three ovov sub-blocks) are
-// staged in shared memory, with the orbit's virtual energies in FP64 and as
-// FP32 offsets from their block origins.
+// Mixed-precision epilogue: the same block-orbit algorithm on 8^3 cubes of
+// FP32 W, as a persistent kernel (2 CTAs per SM) with two producer warps and a
+// ring of two orbit stages in shared memory.
+//
+// The tensor-core contractions store each group tensor as its term of W in
+// W's own index order, in swizzled 8^3 cubes (tcorr_internal.cuh), so the
+// three cubes that make up one W cube sit at the same cube coordinates and
+// W = C0 + C1 + C2 element by element, and the three terms of a cube are
+// stored side by side.  Per orbit two producer warps issue bulk copies
+// (cp.async.bulk) into a free stage, all completing on the stage's mbarrier:
+// one 6 KB copy per distinct slot (6 for three distinct blocks), the 27 8x8
+// ovov sub-blocks (256 B each, from the blocked FP32 copy), the 9 t1 rows
+// and the 3 blocks of float-float virtual energies, the lanes of a warp side
+// by side.  The copy issue rate per warp bounds the pipeline: one producer
+// warp with 2 KB cubes (57 copies per orbit) measured 0.38 ms per task at
+// o=50, v=450, two warps 0.31 ms.  (The small operands as 16-byte cp.async
+// over the lanes measured 17% slower than bulk copies.)  Eight compute warps
+// evaluate the orbit held in the other stage meanwhile.  The
+// cube swizzle makes every W read conflict-free, and the index arithmetic
+// per element orbit is a handful of precomputed offsets.
+//
+// The per-orbit sum over the CTA goes through shared memory in a fixed
+// order, summed by one compute warp per orbit in rotation, with
+// mbarriers instead of CTA barriers: every wait here is bounded (a wait
+// that expires sets the error flag, the other roles see the abort flag,
+// and the producer lets its copies in flight land before it returns).
 //
 // Precision of the energy terms (the numerators are FP32; denominators, their
 // reciprocals, the products with them and all sums to FP64 accuracy):
@@ -357,65 +353,71 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
 //    fixed order), converted to FP64 once per orbit; the orbit partials of a
 //    task are summed in FP64 (Kahan) by the task reduction.
 constexpr int F8 = 8;
-constexpr int FP0 = 69, FP1 = 8;    // plane / row pitch of a cube: at most 2-way bank conflicts
-constexpr int FSLOT = F8 * FP0;     // floats per cube slot
-#ifndef EPI_F32_CTAS
-#define EPI_F32_CTAS 5
+constexpr int EPI_CW = NT / 32;                 // compute warps
+#ifndef EPI_F32_PRODUCERS
+#define EPI_F32_PRODUCERS 2
 #endif
+constexpr int EPI_PRODUCERS = EPI_F32_PRODUCERS;  // producer warps: the U cubes; the small operands
+static_assert(EPI_PRODUCERS == 1 || EPI_PRODUCERS == 2, "one or two producer warps");
+constexpr int EPI_THREADS = NT + 32 * EPI_PRODUCERS;
+#ifndef EPI_F32_STAGES
+#define EPI_F32_STAGES 2
+#endif
+#ifndef EPI_F32_CTAS
+#define EPI_F32_CTAS 2
+#endif
+constexpr int EPI_STAGES = EPI_F32_STAGES;      // orbit stages in shared memory (44 KB each)
+constexpr int EPI_CTAS = EPI_F32_CTAS;          // CTAs per SM
 
-__global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wave wv) {
-    __shared__ float Ws[6 * FSLOT];
-    __shared__ float T1s[3][3][F8];          // [occupied i,j,k][orbit block][local]
-    __shared__ __align__(16) float OVs[3][3][3][F8 * F8];  // [(jk),(ik),(ij)][block][block][8x8]
-    __shared__ ff Evs[3][F8];                // [orbit block][local] virtual energies (float-float)
-    __shared__ ff eijk_s;                    // e_i + e_j + e_k (float-float)
+struct EpiStage {
+    float cube[6][3][512];       // [slot][group]: the three terms of the slot's W cube (as stored in U)
+    float ov[3][3][3][F8 * F8];  // [(j y|k z), (i x|k z), (i x|j y)][block][block][8x8]
+    float t1[3][3][F8];          // [occupied i, j, k][orbit block][local]
+    float2 ev[3][F8];            // [orbit block][local] eps_v as float-float (hi, lo)
+};
+static_assert(sizeof(EpiStage) % 16 == 0, "stages keep 16-byte alignment");
+constexpr size_t EPI_SMEM = EPI_STAGES * sizeof(EpiStage);
+
+struct EpiMeta {
+    double *out;                 // the orbit's (E4, E5) partial
+    ff eijk;                     // e_i + e_j + e_k
+    int ob[3];                   // blocks A <= B <= C
+    int smap[6];                 // slot whose cubes hold slot s's data (the first with its block triple)
+    int kind;                    // 0: no more orbits, 1: three distinct blocks, 2: repeated blocks
+    int v;                       // virtual orbitals of the problem
+};
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(EPI_THREADS, EPI_CTAS) epilogue_f32_kernel(const __grid_constant__ Wave wv) {
+    using namespace tcx;
+    extern __shared__ __align__(128) unsigned char epi_smem[];
+    EpiStage *stg = reinterpret_cast<EpiStage *>(epi_smem);
+    __shared__ EpiMeta meta[EPI_STAGES];
+    __shared__ __align__(8) uint64_t bar_full[EPI_STAGES], bar_empty[EPI_STAGES];
+    __shared__ __align__(8) uint64_t bar_rfull[2], bar_rempty[2];
+    __shared__ __align__(16) float4 red[2][NT];
     __shared__ int comp[6][6];
-    __shared__ int distinct[6];
-    __shared__ ff red[NT][2];
+    __shared__ volatile int abort_sh;
 
-    const int64_t item = blockIdx.x;
-    const Seg sg = wv.segs[seg_find(wv.segs, wv.nseg, item, [](const Seg &x) { return x.epi0; })];
-    const InstDesc &p = wv.descs[sg.inst];
-    const int o = p.dm.o, v = p.dm.v, vc = p.dm.vc;
-    const int64_t v2 = (int64_t)v * v;
-    const int tb = (int)((item - sg.epi0) / p.norb), orb = (int)((item - sg.epi0) % p.norb);
-    const int tid = threadIdx.x;
-    const int *tk = p.tasks + 3 * (sg.task0 + tb);
-    const int ti = tk[0], tj = tk[1], tkk = tk[2];
-    double *out = wv.partials + sg.part_off + ((int64_t)tb * p.norb + orb) * 2;
-    if (ti == tj && tj == tkk) {
-        if (tid == 0) { out[0] = 0.0; out[1] = 0.0; }
-        return;
-    }
-    // every thread reads the orbit's blocks itself (no shared-memory round trip),
-    // so the U loads below can be issued before any barrier
-    const int ob0 = p.orbits[3 * orb], ob1 = p.orbits[3 * orb + 1], ob2 = p.orbits[3 * orb + 2];
-#define OBP(s, d) pick3(ob0, ob1, ob2, perm_pos((s), (d)))
-
-    // W[x][y][z] = S0[x][y][z] + S1[x][y][z] + S2[z][x][y]: slots 0 and 1 read
-    // along z, slot 2 along y (all rows contiguous); the loads are issued first
-    // and consumed after the Y operands have been staged.
-    const float *S0 = static_cast<const float *>(wv.U) + sg.u_off + (int64_t)(tb * 3 + 0) * v2 * vc;
-    const int64_t gs = v2 * vc;
-    float4 ra[3], rb[3], rc[3];
-#pragma unroll
-    for (int it = 0; it < 3; it++) {
-        const int idx = tid + it * NT;            // 6 slots x 64 rows x 2 halves = 768
-        const int s = idx >> 7, row = (idx >> 1) & 63, hf = idx & 1;
-        const int x = OBP(s, 0) * F8 + (row >> 3), y = OBP(s, 1) * F8 + (row & 7);
-        const int z0 = OBP(s, 2) * F8 + hf * 4;
-        ra[it] = rb[it] = rc[it] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (x < v && y < v && z0 < v) {
-            const float4 *q = reinterpret_cast<const float4 *>(S0 + ((int64_t)x * v + y) * vc + z0);
-            ra[it] = __ldg(q);
-            rb[it] = __ldg(q + gs / 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < EPI_STAGES; s++) {
+            mbar_init(smem_u32(&bar_full[s]), EPI_PRODUCERS);  // one expect_tx arrival per producer warp
+            mbar_init(smem_u32(&bar_empty[s]), EPI_CW);
         }
-        const int z = OBP(s, 2) * F8 + (row >> 3), x2 = OBP(s, 0) * F8 + (row & 7);
-        const int y0 = OBP(s, 1) * F8 + hf * 4;
-        if (z < v && x2 < v && y0 < v)
-            rc[it] = __ldg(reinterpret_cast<const float4 *>(S0 + 2 * gs + ((int64_t)z * v + x2) * vc + y0));
+        for (int b = 0; b < 2; b++) {
+            mbar_init(smem_u32(&bar_rfull[b]), EPI_CW);
+            mbar_init(smem_u32(&bar_rempty[b]), 1);
+        }
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-
     if (tid < 36) {  // comp[pi][q]: the slot of permutation pi composed with q
         const int pi = tid / 6, q = tid % 6;
         const int t0 = perm_pos(pi, perm_pos(q, 0)), t1v = perm_pos(pi, perm_pos(q, 1));
@@ -424,153 +426,339 @@ __global__ void __launch_bounds__(NT, EPI_F32_CTAS) epilogue_f32_kernel(const Wa
             if (perm_pos(s, 0) == t0 && perm_pos(s, 1) == t1v) sig = s;
         comp[pi][q] = sig;
     }
-    if (tid >= 64 && tid < 70) {
-        const int t = tid - 64;
-        int d = 1;
-        for (int s = 0; s < t; s++)
-            if (OBP(s, 0) == OBP(t, 0) && OBP(s, 1) == OBP(t, 1) && OBP(s, 2) == OBP(t, 2)) d = 0;
-        distinct[t] = d;
-    }
-    if (tid == 96) eijk_s = ff_of(p.eps_o[ti] + p.eps_o[tj] + p.eps_o[tkk]);
-    // stage t1, ovov sub-blocks and block-relative energies.  The FP32 inputs
-    // are zero padded to vp (t1 rows [p][x], ovov slabs [p][q][x][z]): every
-    // orbit block lies inside, and a sub-block row is two aligned float4 loads.
-    const int vp = (v + F8 - 1) / F8 * F8;
-    const float *t1 = static_cast<const float *>(p.t1);
-    const float *ov = static_cast<const float *>(p.ovov);
-    if (tid < 3 * 3 * F8) {
-        const int oc = tid / (3 * F8), b = (tid / F8) % 3, m = tid % F8;
-        const int occ = oc == 0 ? ti : (oc == 1 ? tj : tkk);
-        T1s[oc][b][m] = t1[occ * vp + pick3(ob0, ob1, ob2, b) * F8 + m];
-    } else if (tid >= 96 + 32 && tid < 96 + 32 + 3 * F8) {
-        const int e = tid - 128, b = e / F8, m = e % F8, x = pick3(ob0, ob1, ob2, b) * F8 + m;
-        Evs[b][m] = ff_of(x < v ? p.eps_v[x] : 0.0);
-    }
-    // slices: 0 = (j y | k z), 1 = (i x | k z), 2 = (i x | j y); 3 x 9 sub-blocks
-    // x 8 rows x 2 halves = 432 float4
-    for (int e = tid; e < 3 * 9 * F8 * 2; e += NT) {
-        const int sl = e / 144, rem = e - sl * 144, bb = rem >> 4, m = (rem >> 1) & 7, h = rem & 1;
-        const int ba = bb / 3, bc = bb - 3 * ba;
-        const int r = pick3(ob0, ob1, ob2, ba) * F8 + m, c = pick3(ob0, ob1, ob2, bc) * F8 + 4 * h;
-        const int first = sl == 0 ? tj : ti, second = sl == 2 ? tj : tkk;
-        const float4 val = __ldg(reinterpret_cast<const float4 *>(ov + ((int64_t)(first * o + second) * vp + r) * vp + c));
-        *reinterpret_cast<float4 *>(&OVs[sl][ba][bc][m * F8 + 4 * h]) = val;
-    }
+    __syncthreads();  // the last CTA-wide barrier: from here on the roles meet only at mbarriers
 
+    if (warp >= EPI_CW) {
+        const int pw = warp - EPI_CW;  // 0: meta and U cubes; last: the small operands
+        // ---------------- producer warp ----------------
+        // Every lane runs the same decode (uniform loads).  The segment's and
+        // the task's fields live in registers and are reloaded only when they
+        // change; the next item's orbit triple is loaded one item ahead, so no
+        // dependent global load sits on the path of an orbit's copies.
+        int si = -1, tb_c = -1, n = 0;
+        int tb_at = 0, orb_at = 0;  // (task, orbit) of the item at hand, advanced by gridDim.x per item
+        int64_t sbeg = 0, send = 0, task0 = 0, part_off = 0;
+        int o = 0, v = 0, nb = 0, norb = 1;
+        int64_t ug = 0;
+        const int *tasks = nullptr, *orbits = nullptr;
+        const double *eps_o = nullptr;
+        const float *Useg = nullptr, *ovf = nullptr, *t1f = nullptr;
+        const float2 *evf = nullptr;
+        int ti = 0, tj = 0, tkk = 0;
+        ff eijk = {0.f, 0.f};
+        int pf_orb = -1, pf0 = 0, pf1 = 0, pf2 = 0;  // prefetched orbit triple (current segment)
+        bool ok = true;
+        for (int64_t it = blockIdx.x; it < wv.n_epi && ok; it += gridDim.x) {
+            if (si < 0 || it >= send) {
+                si = seg_find(wv.segs, wv.nseg, it, [](const Seg &x) { return x.epi0; });
+                const Seg sg = wv.segs[si];
+                const InstDesc &p = wv.descs[sg.inst];
+                sbeg = sg.epi0;
+                send = si + 1 < wv.nseg ? wv.segs[si + 1].epi0 : wv.n_epi;
+                task0 = sg.task0;
+                part_off = sg.part_off;
+                o = p.dm.o;
+                v = p.dm.v;
+                nb = (v + F8 - 1) / F8;
+                norb = p.norb;
+                ug = p.dm.ug;
+                tasks = p.tasks;
+                orbits = p.orbits;
+                Useg = static_cast<const float *>(wv.U) + sg.u_off;
+                ovf = static_cast<const float *>(p.ovov);
+                t1f = static_cast<const float *>(p.t1);
+                evf = p.evf;
+                eps_o = p.eps_o;
+                tb_c = -1;
+                pf_orb = -1;
+                tb_at = (int)((it - sbeg) / norb);
+                orb_at = (int)((it - sbeg) % norb);
+            }
+            const int tb = tb_at, orb = orb_at;
+            int ob0, ob1, ob2;
+            if (pf_orb == orb) {
+                ob0 = pf0; ob1 = pf1; ob2 = pf2;
+            } else {
+                ob0 = orbits[3 * orb]; ob1 = orbits[3 * orb + 1]; ob2 = orbits[3 * orb + 2];
+            }
+            // the next item's (task, orbit), and its triple when it lies in this segment
+            orb_at += gridDim.x;
+            if (orb_at >= norb) {
+                const int q = orb_at / norb;
+                tb_at += q;
+                orb_at -= q * norb;
+            }
+            pf_orb = -1;
+            if (it + gridDim.x < send) {
+                pf_orb = orb_at;
+                pf0 = orbits[3 * pf_orb]; pf1 = orbits[3 * pf_orb + 1]; pf2 = orbits[3 * pf_orb + 2];
+            }
+            if (tb != tb_c) {
+                const int *tk = tasks + 3 * (task0 + tb);
+                ti = tk[0]; tj = tk[1]; tkk = tk[2];
+                if (!(ti == tj && tj == tkk)) eijk = ff_of(eps_o[ti] + eps_o[tj] + eps_o[tkk]);
+                tb_c = tb;
+            }
+            double *out = wv.partials + part_off + ((int64_t)tb * norb + orb) * 2;
+            if (ti == tj && tj == tkk) {  // no energy: nothing to load
+                if (lane == 0) { out[0] = 0.0; out[1] = 0.0; }
+                continue;
+            }
+            const int stage = n % EPI_STAGES;
+            if (n >= EPI_STAGES &&
+                !mbar_wait(smem_u32(&bar_empty[stage]), (uint32_t)((n / EPI_STAGES - 1) & 1), &abort_sh)) {
+                if (lane == 0) fail(&abort_sh, wv.err, DERR_TIMEOUT_EMPTY);
+                ok = false;
+                break;
+            }
+            // slot s holds the cube with block pick3(ob, perm_pos(s, d)) along axis d;
+            // a slot whose triple repeats an earlier one's is not loaded
+            int smap[6], loaded = 0, nload = 0;
 #pragma unroll
-    for (int it = 0; it < 3; it++) {
-        const int idx = tid + it * NT;
-        const int s = idx >> 7, row = (idx >> 1) & 63, hf = idx & 1;
-        const int z0 = OBP(s, 2) * F8 + hf * 4;
-        float *wrow = Ws + s * FSLOT + (row >> 3) * FP0 + (row & 7) * FP1 + hf * 4;
-        const float w[4] = {ra[it].x + rb[it].x, ra[it].y + rb[it].y, ra[it].z + rb[it].z, ra[it].w + rb[it].w};
+            for (int s = 0; s < 6; s++) {
+                smap[s] = s;
 #pragma unroll
-        for (int m = 0; m < 4; m++) wrow[m] = (z0 + m < v) ? w[m] : 0.f;  // U row padding is not data
-    }
-    __syncthreads();
+                for (int t = s - 1; t >= 0; t--)
+                    if (pick3(ob0, ob1, ob2, perm_pos(t, 0)) == pick3(ob0, ob1, ob2, perm_pos(s, 0)) &&
+                        pick3(ob0, ob1, ob2, perm_pos(t, 1)) == pick3(ob0, ob1, ob2, perm_pos(s, 1)) &&
+                        pick3(ob0, ob1, ob2, perm_pos(t, 2)) == pick3(ob0, ob1, ob2, perm_pos(s, 2)))
+                        smap[s] = t;
+                if (smap[s] == s) { loaded |= 1 << s; nload++; }
+            }
+            const uint32_t full = smem_u32(&bar_full[stage]);
+            // the copies of an orbit: e in [0, 6) the U cubes of slot e (the three
+            // group terms, 6 KB); [6, 33) the 27 ovov sub-blocks (256 B);
+            // [33, 42) the 9 t1 rows (32 B); [42, 45) the 3 energy blocks (64 B).
+            // Two producer warps: warp 0 takes the cubes, t1 and energies (and
+            // writes the stage's meta), warp 1 the ovov sub-blocks.
+            constexpr uint32_t ov_bytes = 27 * 256, te_bytes = 9 * 32 + 3 * 64;
+            const uint32_t u_bytes = (uint32_t)nload * 3 * 2048;
+            if (lane == 0 && pw != 0) mbar_expect_tx(full, ov_bytes);
+            if (lane == 0 && pw == 0) {
+                EpiMeta &m = meta[stage];
+                m.out = out;
+                m.eijk = eijk;
+                m.ob[0] = ob0; m.ob[1] = ob1; m.ob[2] = ob2;
 #pragma unroll
-    for (int it = 0; it < 3; it++) {
-        const int idx = tid + it * NT;
-        const int s = idx >> 7, row = (idx >> 1) & 63, hf = idx & 1;
-        const int lz = row >> 3, lx = row & 7;
-        const int y0 = OBP(s, 1) * F8 + hf * 4;
-        const float w[4] = {rc[it].x, rc[it].y, rc[it].z, rc[it].w};
-#pragma unroll
-        for (int m = 0; m < 4; m++)
-            if (y0 + m < v) Ws[s * FSLOT + lx * FP0 + (hf * 4 + m) * FP1 + lz] += w[m];
-    }
-    __syncthreads();
-
-    const ff eijk = eijk_s;
-    ff A4 = {0.f, 0.f}, A5 = {0.f, 0.f};
-    if (ob0 < ob1 && ob1 < ob2) {
-        // Distinct blocks: each thread takes element orbits, the six orderings
-        // of one (a,b,c) with a in A, b in B, c in C.  Slot q holds the element
-        // with indices ordered as q (slots 0..5 = abc, acb, bac, bca, cab, cba);
-        // even slots 0,3,4, odd slots 1,2,5.  With E and O the sums of W over
-        // the even and odd slots, Z at slot q is 6 w_q + 2E - 4O (q even) or
-        // 6 w_q + 2O - 4E (q odd), and all six share one denominator.
-        // thread: fixed (b, c) = (lb, lc), a = la0 and la0 + 4 (the 512 element
-        // orbits of the cube over 256 threads); what depends only on b and c is
-        // read once
-        const int A0 = ob0 * F8, B0 = ob1 * F8, C0 = ob2 * F8;
-        const int lb = (tid >> 3) & 7, lc = tid & 7, la0 = tid >> 6;
-#define OVV(sl, pu, pw, lu, lw) OVs[sl][pu][pw][(lu) * F8 + (lw)]
-        const float tib = T1s[0][1][lb], tic = T1s[0][2][lc];
-        const float tjb = T1s[1][1][lb], tjc = T1s[1][2][lc];
-        const float tkb = T1s[2][1][lb], tkc = T1s[2][2][lc];
-        const float jk_bc = OVV(0, 1, 2, lb, lc), jk_cb = OVV(0, 2, 1, lc, lb);
-        const float ik_bc = OVV(1, 1, 2, lb, lc), ik_cb = OVV(1, 2, 1, lc, lb);
-        const float ij_bc = OVV(2, 1, 2, lb, lc), ij_cb = OVV(2, 2, 1, lc, lb);
-        const ff dbc = ff_sub(ff_sub(eijk, Evs[1][lb]), Evs[2][lc]);
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int la = la0 + 4 * h;
-            if (A0 + la >= v || B0 + lb >= v || C0 + lc >= v) break;  // a grows with h
-            const float w0 = Ws[0 * FSLOT + la * FP0 + lb * FP1 + lc];
-            const float w1 = Ws[1 * FSLOT + la * FP0 + lc * FP1 + lb];
-            const float w2 = Ws[2 * FSLOT + lb * FP0 + la * FP1 + lc];
-            const float w3 = Ws[3 * FSLOT + lb * FP0 + lc * FP1 + la];
-            const float w4 = Ws[4 * FSLOT + lc * FP0 + la * FP1 + lb];
-            const float w5 = Ws[5 * FSLOT + lc * FP0 + lb * FP1 + la];
-            // t1 of occupied i, j, k at a (at b and c above)
-            const float tia = T1s[0][0][la], tja = T1s[1][0][la], tka = T1s[2][0][la];
-            // (j u | k w), (i u | k w), (i u | j w) for the ordered pairs of {a, b, c} that hold a
-            const float jk_ac = OVV(0, 0, 2, la, lc), jk_ca = OVV(0, 2, 0, lc, la);
-            const float jk_ab = OVV(0, 0, 1, la, lb), jk_ba = OVV(0, 1, 0, lb, la);
-            const float ik_ac = OVV(1, 0, 2, la, lc), ik_ca = OVV(1, 2, 0, lc, la);
-            const float ik_ab = OVV(1, 0, 1, la, lb), ik_ba = OVV(1, 1, 0, lb, la);
-            const float ij_ac = OVV(2, 0, 2, la, lc), ij_ca = OVV(2, 2, 0, lc, la);
-            const float ij_ab = OVV(2, 0, 1, la, lb), ij_ba = OVV(2, 1, 0, lb, la);
-            // Y at each ordering q of (a,b,c): t^{q0}_i (j q1|k q2) + t^{q1}_j (i q0|k q2) + t^{q2}_k (i q0|j q1)
-            const float y0 = tia * jk_bc + tjb * ik_ac + tkc * ij_ab;
-            const float y1 = tia * jk_cb + tjc * ik_ab + tkb * ij_ac;
-            const float y2 = tib * jk_ac + tja * ik_bc + tkc * ij_ba;
-            const float y3 = tib * jk_ca + tjc * ik_ba + tka * ij_bc;
-            const float y4 = tic * jk_ab + tja * ik_cb + tkb * ij_ca;
-            const float y5 = tic * jk_ba + tjb * ik_ca + tka * ij_cb;
-            const float E = w0 + w3 + w4, O = w1 + w2 + w5;
-            const float ww = w0 * w0 + w1 * w1 + w2 * w2 + w3 * w3 + w4 * w4 + w5 * w5;
-            const float wy = w0 * y0 + w1 * y1 + w2 * y2 + w3 * y3 + w4 * y4 + w5 * y5;
-            const float s4 = 6.f * ww + 2.f * (E * E + O * O) - 8.f * E * O;
-            const float s5 = 6.f * wy + (2.f * E - 4.f * O) * (y0 + y3 + y4) + (2.f * O - 4.f * E) * (y1 + y2 + y5);
-            const ff r = ff_recip(ff_sub(dbc, Evs[0][la]));
-            A4 = ff_add(A4, ff_mul(s4, r));
-            A5 = ff_add(A5, ff_mul(s5, r));
+                for (int s = 0; s < 6; s++) m.smap[s] = smap[s];
+                m.kind = (ob0 < ob1 && ob1 < ob2) ? 1 : 2;
+                m.v = v;
+                mbar_expect_tx(full, u_bytes + te_bytes + (EPI_PRODUCERS == 1 ? ov_bytes : 0u));
+            }
+            __syncwarp();
+            const float *Ut = Useg + (int64_t)tb * 3 * ug;
+            const uint32_t sb = smem_u32(&stg[stage]);
+            const int ncopy = EPI_PRODUCERS == 1 ? 45 : (pw == 0 ? 18 : 27);
+            for (int k = lane; k < ncopy; k += 32) {
+                const int e = EPI_PRODUCERS == 1 ? k : (pw == 0 ? (k < 6 ? k : k + 27) : k + 6);
+                if (e < 6) {
+                    if (!((loaded >> e) & 1)) continue;
+                    const int X = pick3(ob0, ob1, ob2, perm_pos(e, 0)), Y = pick3(ob0, ob1, ob2, perm_pos(e, 1)),
+                              Z = pick3(ob0, ob1, ob2, perm_pos(e, 2));
+                    bulk_load(sb + (uint32_t)offsetof(EpiStage, cube) + (uint32_t)e * 6144u,
+                              Ut + (((int64_t)X * nb + Y) * nb + Z) * 3 * 512, 6144u, full);
+                } else if (e < 33) {
+                    const int q = e - 6, sl = q / 9, ba = (q / 3) % 3, bc = q % 3;
+                    const int first = sl == 0 ? tj : ti, second = sl == 2 ? tj : tkk;
+                    const int X = pick3(ob0, ob1, ob2, ba), Z = pick3(ob0, ob1, ob2, bc);
+                    bulk_load(sb + (uint32_t)offsetof(EpiStage, ov) + (uint32_t)q * 256u,
+                              ovf + ((((int64_t)first * o + second) * nb + X) * nb + Z) * 64, 256u, full);
+                } else if (e < 42) {
+                    const int q = e - 33, oc = q / 3, b = q - 3 * oc;
+                    const int occ = oc == 0 ? ti : (oc == 1 ? tj : tkk);
+                    bulk_load(sb + (uint32_t)offsetof(EpiStage, t1) + (uint32_t)q * 32u,
+                              t1f + (int64_t)occ * nb * F8 + pick3(ob0, ob1, ob2, b) * F8, 32u, full);
+                } else {
+                    const int b = e - 42;
+                    bulk_load(sb + (uint32_t)offsetof(EpiStage, ev) + (uint32_t)b * 64u,
+                              evf + pick3(ob0, ob1, ob2, b) * F8, 64u, full);
+                }
+            }
+            n++;
         }
+        if (ok) {  // end marker
+            const int stage = n % EPI_STAGES;
+            if (n >= EPI_STAGES &&
+                !mbar_wait(smem_u32(&bar_empty[stage]), (uint32_t)((n / EPI_STAGES - 1) & 1), &abort_sh)) {
+                if (lane == 0) fail(&abort_sh, wv.err, DERR_TIMEOUT_EMPTY);
+                ok = false;
+            } else if (lane == 0) {
+                if (pw == 0) meta[stage].kind = 0;
+                mbar_arrive(smem_u32(&bar_full[stage]));
+            }
+        }
+        if (!ok) {  // let the copies of the stages still in flight land (bounded)
+            volatile int no_abort = 0;
+            for (int m = n - EPI_STAGES < 0 ? 0 : n - EPI_STAGES; m < n; m++)
+                mbar_wait(smem_u32(&bar_full[m % EPI_STAGES]), (uint32_t)((m / EPI_STAGES) & 1), &no_abort);
+        }
+        return;
+    }
+
+    // ---------------- compute warps ----------------
+    // thread: fixed (b, c) = (lb, lc), a = la0 and la0 + 4 (the 512 element
+    // orbits of a cube with three distinct blocks over 256 threads)
+    const int lb = (tid >> 3) & 7, lc = tid & 7, la0 = tid >> 6;
+    // cube offsets of the six orderings (abc, acb, bac, bca, cab, cba) in C0
+    // and C1 (offd) and in C2 (offd2: its y index innermost)
+    int offd[2][6], offd2[2][6];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int la = la0 + 4 * h;
+        offd[h][0] = ucube_off(la, lb, lc);
+        offd[h][1] = ucube_off(la, lc, lb);
+        offd[h][2] = ucube_off(lb, la, lc);
+        offd[h][3] = ucube_off(lb, lc, la);
+        offd[h][4] = ucube_off(lc, la, lb);
+        offd[h][5] = ucube_off(lc, lb, la);
+        offd2[h][0] = ucube_off(la, lc, lb);
+        offd2[h][1] = ucube_off(la, lb, lc);
+        offd2[h][2] = ucube_off(lb, lc, la);
+        offd2[h][3] = ucube_off(lb, la, lc);
+        offd2[h][4] = ucube_off(lc, lb, la);
+        offd2[h][5] = ucube_off(lc, la, lb);
+    }
+    for (int n = 0;; n++) {
+        const int stage = n % EPI_STAGES;
+        if (!mbar_wait(smem_u32(&bar_full[stage]), (uint32_t)((n / EPI_STAGES) & 1), &abort_sh)) {
+            if (lane == 0) fail(&abort_sh, wv.err, DERR_TIMEOUT_FULL);
+            return;
+        }
+        const int kind = meta[stage].kind;
+        if (kind == 0) return;
+        double *const out = meta[stage].out;
+        const ff eijk = meta[stage].eijk;
+        const int ob0 = meta[stage].ob[0], ob1 = meta[stage].ob[1], ob2 = meta[stage].ob[2];
+        const int v = meta[stage].v;
+        const EpiStage &S = stg[stage];
+        ff A4 = {0.f, 0.f}, A5 = {0.f, 0.f};
+        if (kind == 1) {
+            // Distinct blocks: each thread takes element orbits, the six orderings
+            // of one (a,b,c) with a in A, b in B, c in C.  Slot q holds the element
+            // with indices ordered as q (slots 0..5 = abc, acb, bac, bca, cab, cba);
+            // even slots 0,3,4, odd slots 1,2,5.  With E and O the sums of W over
+            // the even and odd slots, Z at slot q is 6 w_q + 2E - 4O (q even) or
+            // 6 w_q + 2O - 4E (q odd), and all six share one denominator.  What
+            // depends only on b and c is read once for the thread's two orbits.
+            const int A0 = ob0 * F8, B0 = ob1 * F8, C0 = ob2 * F8;
+#define OVV(sl, pu, pw, lu, lw) S.ov[sl][pu][pw][(lu) * F8 + (lw)]
+#define WQ(q, h) (S.cube[q][0][offd[h][q]] + S.cube[q][1][offd[h][q]] + S.cube[q][2][offd2[h][q]])
+            const float tib = S.t1[0][1][lb], tic = S.t1[0][2][lc];
+            const float tjb = S.t1[1][1][lb], tjc = S.t1[1][2][lc];
+            const float tkb = S.t1[2][1][lb], tkc = S.t1[2][2][lc];
+            const float jk_bc = OVV(0, 1, 2, lb, lc), jk_cb = OVV(0, 2, 1, lc, lb);
+            const float ik_bc = OVV(1, 1, 2, lb, lc), ik_cb = OVV(1, 2, 1, lc, lb);
+            const float ij_bc = OVV(2, 1, 2, lb, lc), ij_cb = OVV(2, 2, 1, lc, lb);
+            const ff evb = {S.ev[1][lb].x, S.ev[1][lb].y}, evc = {S.ev[2][lc].x, S.ev[2][lc].y};
+            const ff dbc = ff_sub(ff_sub(eijk, evb), evc);
+            const bool bc_in = B0 + lb < v && C0 + lc < v;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int la = la0 + 4 * h;
+                if (!bc_in || A0 + la >= v) break;  // a grows with h
+                const float w0 = WQ(0, h), w1 = WQ(1, h), w2 = WQ(2, h);
+                const float w3 = WQ(3, h), w4 = WQ(4, h), w5 = WQ(5, h);
+                // t1 of occupied i, j, k at a (at b and c above)
+                const float tia = S.t1[0][0][la], tja = S.t1[1][0][la], tka = S.t1[2][0][la];
+                // (j u | k w), (i u | k w), (i u | j w) for the ordered pairs of {a, b, c} that hold a
+                const float jk_ac = OVV(0, 0, 2, la, lc), jk_ca = OVV(0, 2, 0, lc, la);
+                const float jk_ab = OVV(0, 0, 1, la, lb), jk_ba = OVV(0, 1, 0, lb, la);
+                const float ik_ac = OVV(1, 0, 2, la, lc), ik_ca = OVV(1, 2, 0, lc, la);
+                const float ik_ab = OVV(1, 0, 1, la, lb), ik_ba = OVV(1, 1, 0, lb, la);
+                const float ij_ac = OVV(2, 0, 2, la, lc), ij_ca = OVV(2, 2, 0, lc, la);
+                const float ij_ab = OVV(2, 0, 1, la, lb), ij_ba = OVV(2, 1, 0, lb, la);
+                // Y at each ordering q of (a,b,c): t^{q0}_i (j q1|k q2) + t^{q1}_j (i q0|k q2) + t^{q2}_k (i q0|j q1)
+                const float y0 = tia * jk_bc + tjb * ik_ac + tkc * ij_ab;
+                const float y1 = tia * jk_cb + tjc * ik_ab + tkb * ij_ac;
+                const float y2 = tib * jk_ac + tja * ik_bc + tkc * ij_ba;
+                const float y3 = tib * jk_ca + tjc * ik_ba + tka * ij_bc;
+                const float y4 = tic * jk_ab + tja * ik_cb + tkb * ij_ca;
+                const float y5 = tic * jk_ba + tjb * ik_ca + tka * ij_cb;
+                const float E = w0 + w3 + w4, O = w1 + w2 + w5;
+                const float ww = w0 * w0 + w1 * w1 + w2 * w2 + w3 * w3 + w4 * w4 + w5 * w5;
+                const float wy = w0 * y0 + w1 * y1 + w2 * y2 + w3 * y3 + w4 * y4 + w5 * y5;
+                const float s4 = 6.f * ww + 2.f * (E * E + O * O) - 8.f * E * O;
+                const float s5 = 6.f * wy + (2.f * E - 4.f * O) * (y0 + y3 + y4) + (2.f * O - 4.f * E) * (y1 + y2 + y5);
+                const ff eva = {S.ev[0][la].x, S.ev[0][la].y};
+                const ff r = ff_recip(ff_sub(dbc, eva));
+                A4 = ff_add(A4, ff_mul(s4, r));
+                A5 = ff_add(A5, ff_mul(s5, r));
+            }
+#undef WQ
 #undef OVV
-    } else {
-        // blocks repeat: element by element over the distinct cube slots
-        for (int s = 0; s < 6; s++) {
-            if (!distinct[s]) continue;
-            const int p0 = perm_pos(s, 0), p1 = perm_pos(s, 1), p2 = perm_pos(s, 2);
-            const float *W0 = Ws + comp[s][0] * FSLOT, *W1 = Ws + comp[s][1] * FSLOT;
-            const float *W2 = Ws + comp[s][2] * FSLOT, *W3 = Ws + comp[s][3] * FSLOT;
-            const float *W4 = Ws + comp[s][4] * FSLOT, *W5 = Ws + comp[s][5] * FSLOT;
-            for (int l = tid; l < 512; l += NT) {
-                const int l0 = l >> 6, l1 = (l >> 3) & 7, l2 = l & 7;
-                const int x = pick3(ob0, ob1, ob2, p0) * F8 + l0, y = pick3(ob0, ob1, ob2, p1) * F8 + l1,
-                          z = pick3(ob0, ob1, ob2, p2) * F8 + l2;
-                if (x >= v || y >= v || z >= v) continue;
-                const float w0 = W0[l0 * FP0 + l1 * FP1 + l2];
-                // Z = 8 W(abc) - 4 (W(acb) + W(bac) + W(cba)) + 2 (W(bca) + W(cab))
-                const float zv = 8.f * w0 -
-                                 4.f * (W1[l0 * FP0 + l2 * FP1 + l1] + W2[l1 * FP0 + l0 * FP1 + l2] +
-                                        W5[l2 * FP0 + l1 * FP1 + l0]) +
-                                 2.f * (W3[l1 * FP0 + l2 * FP1 + l0] + W4[l2 * FP0 + l0 * FP1 + l1]);
-                const float yv = T1s[0][p0][l0] * OVs[0][p1][p2][l1 * F8 + l2] +
-                                 T1s[1][p1][l1] * OVs[1][p0][p2][l0 * F8 + l2] +
-                                 T1s[2][p2][l2] * OVs[2][p0][p1][l0 * F8 + l1];
-                const ff r = ff_recip(ff_sub(ff_sub(ff_sub(eijk, Evs[p0][l0]), Evs[p1][l1]), Evs[p2][l2]));
-                A4 = ff_add(A4, ff_mul(zv * w0, r));
-                A5 = ff_add(A5, ff_mul(zv * yv, r));
+        } else {
+            // blocks repeat: element by element over the distinct slots
+            for (int s = 0; s < 6; s++) {
+                if (meta[stage].smap[s] != s) continue;
+                const int p0 = perm_pos(s, 0), p1 = perm_pos(s, 1), p2 = perm_pos(s, 2);
+                const float *W[6];
+#pragma unroll
+                for (int q = 0; q < 6; q++) W[q] = S.cube[meta[stage].smap[comp[s][q]]][0];
+#define WAT(q, x, y, z) (W[q][ucube_off(x, y, z)] + W[q][512 + ucube_off(x, y, z)] + W[q][1024 + ucube_off(x, z, y)])
+                for (int l = tid; l < 512; l += NT) {
+                    const int l0 = l >> 6, l1 = (l >> 3) & 7, l2 = l & 7;
+                    const int x = pick3(ob0, ob1, ob2, p0) * F8 + l0, y = pick3(ob0, ob1, ob2, p1) * F8 + l1,
+                              z = pick3(ob0, ob1, ob2, p2) * F8 + l2;
+                    if (x >= v || y >= v || z >= v) continue;
+                    const float w0 = WAT(0, l0, l1, l2);
+                    // Z = 8 W(abc) - 4 (W(acb) + W(bac) + W(cba)) + 2 (W(bca) + W(cab))
+                    const float zv = 8.f * w0 - 4.f * (WAT(1, l0, l2, l1) + WAT(2, l1, l0, l2) + WAT(5, l2, l1, l0)) +
+                                     2.f * (WAT(3, l1, l2, l0) + WAT(4, l2, l0, l1));
+                    const float yv = S.t1[0][p0][l0] * S.ov[0][p1][p2][l1 * F8 + l2] +
+                                     S.t1[1][p1][l1] * S.ov[1][p0][p2][l0 * F8 + l2] +
+                                     S.t1[2][p2][l2] * S.ov[2][p0][p1][l0 * F8 + l1];
+                    const ff e0 = {S.ev[p0][l0].x, S.ev[p0][l0].y}, e1 = {S.ev[p1][l1].x, S.ev[p1][l1].y},
+                             e2 = {S.ev[p2][l2].x, S.ev[p2][l2].y};
+                    const ff r = ff_recip(ff_sub(ff_sub(ff_sub(eijk, e0), e1), e2));
+                    A4 = ff_add(A4, ff_mul(zv * w0, r));
+                    A5 = ff_add(A5, ff_mul(zv * yv, r));
+                }
+#undef WAT
+            }
+        }
+        // the stage is free once every warp has read it
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_empty[stage]));
+
+        // sum over the CTA: every thread's pair into red[n & 1], then warp
+        // n % 8 sums the 256 pairs in a fixed order (32 per lane, then a
+        // shuffle tree) and writes the orbit's FP64 partial
+        const int rb = n & 1;
+        if (n >= 2 && !mbar_wait(smem_u32(&bar_rempty[rb]), (uint32_t)(((n >> 1) - 1) & 1), &abort_sh)) {
+            if (lane == 0) fail(&abort_sh, wv.err, DERR_TIMEOUT_EMPTY);
+            return;
+        }
+        red[rb][tid] = make_float4(A4.hi, A4.lo, A5.hi, A5.lo);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_rfull[rb]));
+        if (warp == (n % EPI_CW)) {
+            if (!mbar_wait(smem_u32(&bar_rfull[rb]), (uint32_t)((n >> 1) & 1), &abort_sh)) {
+                if (lane == 0) fail(&abort_sh, wv.err, DERR_TIMEOUT_FULL);
+                return;
+            }
+            float4 t = red[rb][lane];
+            ff b4 = {t.x, t.y}, b5 = {t.z, t.w};
+#pragma unroll
+            for (int k = 1; k < NT / 32; k++) {
+                t = red[rb][lane + 32 * k];
+                b4 = ff_add(b4, ff{t.x, t.y});
+                b5 = ff_add(b5, ff{t.z, t.w});
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const ff c4 = {__shfl_xor_sync(0xffffffffu, b4.hi, off), __shfl_xor_sync(0xffffffffu, b4.lo, off)};
+                const ff c5 = {__shfl_xor_sync(0xffffffffu, b5.hi, off), __shfl_xor_sync(0xffffffffu, b5.lo, off)};
+                b4 = ff_add(b4, c4);
+                b5 = ff_add(b5, c5);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                out[0] = ff_to_double(b4);
+                out[1] = ff_to_double(b5);
+                mbar_arrive(smem_u32(&bar_rempty[rb]));
             }
         }
     }
-    // the orbit partials of a task are summed in FP64 (Kahan) by the task reduction
-    cta_sum2_ff(A4, A5, red, out, tid);
 }
-#undef OBP
 
 // One CTA per task of the wave: Kahan sum of its orbit partials, times m/6.
 __global__ void __launch_bounds__(NT) task_reduce_kernel(const Wave wv) {
@@ -632,15 +820,34 @@ int epilogue_orbits(int v) {
     return nb * (nb + 1) * (nb + 2) / 6;
 }
 
-cudaError_t launch_epilogue(int prec, const Wave &w, cudaStream_t st) {
+cudaError_t epi_prepare() {
+    static std::mutex mu;
+    static bool done = false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(epilogue_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EPI_SMEM);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+cudaError_t launch_epilogue(int prec, int sm_count, const Wave &w, cudaStream_t st) {
     if (w.n_epi <= 0) return cudaSuccess;
     if (w.n_epi > 0x7fffffff) return cudaErrorInvalidConfiguration;
     if (prec == TCORR_FP64) {
         const size_t smem = sizeof(double) * 6 * 8 * 8 * 9;
         epilogue_kernel<double, double, 8><<<(unsigned)w.n_epi, NT, smem, st>>>(w);
-    } else {
-        epilogue_f32_kernel<<<(unsigned)w.n_epi, NT, 0, st>>>(w);
+        return cudaGetLastError();
     }
+    cudaError_t e = epi_prepare();
+    if (e != cudaSuccess) return e;
+    if (sm_count <= 0) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    }
+    const int64_t grid = std::min<int64_t>(w.n_epi, (int64_t)sm_count * EPI_CTAS);
+    epilogue_f32_kernel<<<(unsigned)grid, EPI_THREADS, EPI_SMEM, st>>>(w);
     return cudaGetLastError();
 }
 

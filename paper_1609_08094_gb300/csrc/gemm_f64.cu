@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(NT) ugemm_f64_kernel(const Wave w) {
         __syncthreads();
     }
 
-    double *Ug = static_cast<double *>(w.U) + sg.u_off + (int64_t)(tb * 3 + g) * v2 * vc;
+    double *Ug = static_cast<double *>(w.U) + sg.u_off + (int64_t)(tb * 3 + g) * d.dm.ug;
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         const int a = a0 + ta * 4 + c;

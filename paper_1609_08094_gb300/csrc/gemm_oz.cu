@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ugemm_oz_kernel(const __grid_co
                 const double scale = ldexp(1.0, d.oz_e[0] + d.oz_e[1] - OZ_BETA * (OZ_S + 1));
                 const int a0 = w.n * OZ_N + half * OZ_HALF;
                 const int64_t stride = (int64_t)v * vc;
-                double *Ug = static_cast<double *>(wv.U) + u_seg + (int64_t)(w.tb * 3 + w.g) * v * v * vc +
+                double *Ug = static_cast<double *>(wv.U) + u_seg + (int64_t)(w.tb * 3 + w.g) * d.dm.ug +
                              (int64_t)b * vc + c + (int64_t)a0 * stride;
 #pragma unroll
                 for (int j = 0; j < OZ_HALF; j++) {

@@ -30,8 +30,8 @@
 //             (M = 128, N <= 256, 2 K-steps x 3 products per chunk) into the
 //             accumulator of the current K block of KB = 2 chunks.
 //   warps 2-9: two warps per TMEM lane quarter, 128 columns each: drain each
-//             block into the register total, then store the U rows (rows of
-//             16 consecutive c, coalesced) at the end of the tile.
+//             block into the register total, then store the tile into the
+//             8^3-cube layout of U (whole 32-byte sectors per 8 values of a).
 // A work item is (task, group, pair tile, N pass).  The v values of a are cut
 // into ceil(v / 256) passes of equal width (a multiple of 16, at most 256), so
 // the B tiles carry no more padding rows than the rounding needs.  Every
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
             if (w.diag) continue;
             const InstDesc &d = *sc.d;
             const int64_t u_seg = sc.u_off;
-            const int v = d.dm.v, vc = d.dm.vc;
+            const int v = d.dm.v;
             const int nhb = (num_chunks(d) + d.kb - 1) / d.kb;
             const int lb = row / d.pc, lc = row % d.pc;
             // the two warps of a lane quarter split the accumulator's N columns:
@@ -278,29 +278,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_kernel(const __grid_co
                 if (lane == 0) fail(&abort_sh, wv.err, DERR_TIMEOUT_TMEM);
                 break;
             }
-            // rows of 16 consecutive c per half warp: group 0 and 2 in their own
-            // [a][b][c] order, group 1 at [b][a][c] (aligned with W, see tcorr_internal.cuh)
+            // each group as its term of W, in 8^3 cubes (tcorr_internal.cuh)
             const int b = w.bt * d.pb + lb, c = w.ct * d.pc + lc;
             if (b < v && c < v) {
-                const int a0 = pass0 + half * wh;
-                const int64_t stride = w.g == 1 ? (int64_t)vc : (int64_t)v * vc;
-                const int64_t base = w.g == 1 ? (int64_t)b * v * vc + c : (int64_t)b * vc + c;
-                const int64_t u_off = u_seg + (int64_t)(w.tb * 3 + w.g) * v * v * vc;
-                float *Ug = static_cast<float *>(wv.U) + u_off + base + (int64_t)a0 * stride;
-                const int na = min(wh, pass_end - a0);
-                if (na == 128) {
-#pragma unroll
-                    for (int j = 0; j < 128; j++) {
-                        *Ug = total[j];
-                        Ug += stride;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 128; j++) {
-                        if (j < na) *Ug = total[j];
-                        Ug += stride;
-                    }
-                }
+                const int a0 = pass0 + half * wh;  // a multiple of 8
+                float *Ut = static_cast<float *>(wv.U) + u_seg + (int64_t)w.tb * 3 * d.dm.ug;
+                store_u_cubes(Ut, (v + 7) >> 3, w.g, a0, b, c, min(wh, pass_end - a0), total);
             }
         }
     }
@@ -574,7 +557,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_pair_kernel(const __gr
             if (w.diag) continue;
             const InstDesc &d = *sc.d;
             const int64_t u_seg = sc.u_off;
-            const int v = d.dm.v, vc = d.dm.vc;
+            const int v = d.dm.v;
             const int nhb = (num_chunks(d) + d.kb - 1) / d.kb;
             const int lb = row / d.pc, lc = row % d.pc;
             const int pass0 = w.n * d.brows, pass_end = min(v, pass0 + d.brows);
@@ -618,25 +601,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ugemm_tc_pair_kernel(const __gr
             if (pw.empty) continue;
             const int b = w.bt * d.pb + lb, c = w.ct * d.pc + lc;
             if (b < v && c < v) {
-                const int a0 = pass0 + half * wh;
-                const int64_t stride = w.g == 1 ? (int64_t)vc : (int64_t)v * vc;
-                const int64_t base = w.g == 1 ? (int64_t)b * v * vc + c : (int64_t)b * vc + c;
-                const int64_t u_off = u_seg + (int64_t)(w.tb * 3 + w.g) * v * v * vc;
-                float *Ug = static_cast<float *>(wv.U) + u_off + base + (int64_t)a0 * stride;
-                const int na = min(wh, pass_end - a0);
-                if (na == 128) {
-#pragma unroll
-                    for (int j = 0; j < 128; j++) {
-                        *Ug = total[j];
-                        Ug += stride;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 128; j++) {
-                        if (j < na) *Ug = total[j];
-                        Ug += stride;
-                    }
-                }
+                const int a0 = pass0 + half * wh;  // a multiple of 8
+                float *Ut = static_cast<float *>(wv.U) + u_seg + (int64_t)w.tb * 3 * d.dm.ug;
+                store_u_cubes(Ut, (v + 7) >> 3, w.g, a0, b, c, min(wh, pass_end - a0), total);
             }
         }
     }

@@ -25,7 +25,7 @@ constexpr int NA_VMAX = TCORR_NOALLOC_MAX_V;
 constexpr int NA_TE = 8;                                   // FP64 epilogue cube edge
 constexpr int NA_NB = (NA_VMAX + NA_TE - 1) / NA_TE;
 constexpr int NA_NORB = NA_NB * (NA_NB + 1) * (NA_NB + 2) / 6;
-constexpr size_t NA_U_BYTES = (size_t)3 * NA_VMAX * NA_VMAX * NA_VMAX * sizeof(double);
+constexpr size_t NA_U_BYTES = (size_t)3 * NA_VMAX * NA_VMAX * NA_VMAX * sizeof(double);  // 3 ug <= 3 NA_VMAX^3
 constexpr size_t NA_PART_OFF = NA_U_BYTES;
 constexpr size_t NA_TASK_OFF = NA_PART_OFF + (size_t)NA_NORB * 2 * sizeof(double);
 constexpr size_t NA_ORB_OFF = NA_TASK_OFF + 16;
@@ -35,7 +35,7 @@ constexpr size_t NA_END = NA_DESC_OFF + sizeof(InstDesc);
 static_assert(NA_END <= TCORR_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the declared size");
 static_assert(NA_VMAX % UPAD == 0, "maximum v must be a multiple of the U row padding");
 
-// The scratch: U [3][v][v][vc] doubles, orbit partials [norb][2] doubles,
+// The scratch: U [3][ug] doubles (each group [v][v][vc]), orbit partials [norb][2] doubles,
 // the task (3 ints), the block-orbit table [norb][3] ints, and the work
 // description the shared epilogue kernels read (one segment, one instance).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TCORR_NOALLOC_SCRATCH_BYTES];
@@ -74,7 +74,8 @@ __global__ void noalloc_tables_kernel(const InstDesc d, const Seg sg, InstDesc *
 //   - sum_l (as|lq) t2[p][l][b][c] - sum_l (as|lp) t2[q][l][c][b],
 // with (db|cq) = vvvo[d][b][c][q] and (as|lq) = ooov[l][q][s][a].
 constexpr int CT_P = 128, CT_A = 32, CT_K = 8;
-__global__ void __launch_bounds__(256) ugemm_f64_canon_kernel(int o, int v, int vc, const double *__restrict__ t2,
+__global__ void __launch_bounds__(256) ugemm_f64_canon_kernel(int o, int v, int vc, int64_t ug,
+                                                              const double *__restrict__ t2,
                                                               const double *__restrict__ vvvo,
                                                               const double *__restrict__ ooov, int ti, int tj,
                                                               int tk, double *__restrict__ U) {
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(256) ugemm_f64_canon_kernel(int o, int v, int 
             __syncthreads();
         }
     }
-    double *Ug = U + (int64_t)g * v2 * vc;
+    double *Ug = U + (int64_t)g * ug;
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         const int a = a0 + ta * 4 + c;
@@ -187,7 +188,7 @@ extern "C" tcorr_status tcorr_task_energy_noalloc(int o, int v, const double *ep
     InstDesc *desc = reinterpret_cast<InstDesc *>(sc + NA_DESC_OFF);
     const int nb = (v + NA_TE - 1) / NA_TE;
     InstDesc d{};
-    d.dm = Dims{o, v, round_up(v, KPAD), round_up(o, KPAD), round_up(v, UPAD)};
+    d.dm = make_dims(o, v);
     d.norb = nb * (nb + 1) * (nb + 2) / 6;
     d.eps_o = eps_occ;
     d.eps_v = eps_vir;
@@ -202,7 +203,7 @@ extern "C" tcorr_status tcorr_task_energy_noalloc(int o, int v, const double *ep
     noalloc_tables_kernel<<<1, 128, 0, st>>>(d, sg, desc, seg, task, orbits, nb, i, j, k);
     const int64_t v2 = (int64_t)v * v;
     dim3 grid((unsigned)((v2 + CT_P - 1) / CT_P), (unsigned)((v + CT_A - 1) / CT_A), 3);
-    ugemm_f64_canon_kernel<<<grid, 256, 0, st>>>(o, v, d.dm.vc, t2, vvvo, ooov, i, j, k, U);
+    ugemm_f64_canon_kernel<<<grid, 256, 0, st>>>(o, v, d.dm.vc, d.dm.ug, t2, vvvo, ooov, i, j, k, U);
     Wave w{};
     w.descs = desc;
     w.segs = seg;
@@ -212,7 +213,7 @@ extern "C" tcorr_status tcorr_task_energy_noalloc(int o, int v, const double *ep
     w.n_red = 1;
     w.U = U;
     w.partials = partials;
-    if (launch_epilogue(TCORR_FP64, w, st) != cudaSuccess) return TCORR_ECUDA;
+    if (launch_epilogue(TCORR_FP64, 0, w, st) != cudaSuccess) return TCORR_ECUDA;
     if (launch_task_reduce(w, st) != cudaSuccess) return TCORR_ECUDA;
     return cudaGetLastError() == cudaSuccess ? TCORR_OK : TCORR_ECUDA;
 }

@@ -69,22 +69,36 @@ __global__ void __launch_bounds__(256) transpose_pad_kernel(
     }
 }
 
-// FP32 epilogue inputs of the split-precision paths: (p x | q z) as slabs
-// [p][q][x][z] and t1 as rows [p][x], the virtual extents padded with zeros
-// to vp (a multiple of the epilogue's cube edge), so that every 8-wide row of
-// an orbit's sub-block is two aligned 16-byte loads with no bounds test.
-__global__ void ovov_slabs_kernel(const double *__restrict__ in, float *__restrict__ out, int o, int v,
-                                  int vp) {
+// FP32 epilogue inputs of the split-precision paths, the virtual extents
+// padded with zeros to vp (a multiple of the epilogue's cube edge 8): (p x | q z)
+// as [p][q][X][Z][8][8], so that each of an orbit's 8x8 sub-blocks is one
+// contiguous, aligned 256-byte bulk copy, and t1 as rows [p][x].
+__global__ void ovov_blocks_kernel(const double *__restrict__ in, float *__restrict__ out, int o, int v,
+                                   int vp) {
     const int64_t n = (int64_t)o * o * vp * vp;
+    const int nb = vp / 8;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int z = (int)(i % vp);
-        int64_t r = i / vp;
-        const int x = (int)(r % vp);
-        r /= vp;
+        const int lz = (int)(i & 7), lx = (int)((i >> 3) & 7);
+        int64_t r = i >> 6;
+        const int zb = (int)(r % nb);
+        r /= nb;
+        const int xb = (int)(r % nb);
+        r /= nb;
         const int q = (int)(r % o), pp = (int)(r / o);
+        const int x = xb * 8 + lx, z = zb * 8 + lz;
         out[i] = (x < v && z < v) ? static_cast<float>(in[(((int64_t)pp * v + x) * o + q) * v + z]) : 0.f;
     }
+}
+
+// eps_v as float-float pairs: hi = eps rounded to FP32, lo = the rest rounded
+// to FP32 (about 48 significant bits together); zero for x >= v
+__global__ void eps_ff_kernel(const double *__restrict__ e, float2 *__restrict__ out, int v, int vp) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= vp) return;
+    const double d = x < v ? e[x] : 0.0;
+    const float hi = static_cast<float>(d);
+    out[x] = make_float2(hi, static_cast<float>(d - static_cast<double>(hi)));
 }
 
 __global__ void pad_rows_kernel(const double *__restrict__ in, float *__restrict__ out, int rows, int v,
@@ -119,11 +133,13 @@ cudaError_t launch_transpose_pad(int kind, const double *in, void *out_hi, void 
     return cudaGetLastError();
 }
 
-cudaError_t launch_epilogue_f32_inputs(const double *t1, const double *ovov, float *t1f, float *ovf, int o,
-                                       int v, int vp, cudaStream_t st) {
+cudaError_t launch_epilogue_f32_inputs(const double *t1, const double *ovov, const double *eps_v, float *t1f,
+                                       float *ovf, float2 *evf, int o, int v, int vp, cudaStream_t st) {
+    if (vp % 8 != 0 || vp < v) return cudaErrorInvalidValue;
     const int64_t n = (int64_t)o * o * vp * vp, blocks = (n + 255) / 256;
-    ovov_slabs_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(ovov, ovf, o, v, vp);
+    ovov_blocks_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(ovov, ovf, o, v, vp);
     pad_rows_kernel<<<(unsigned)((o * (int64_t)vp + 255) / 256), 256, 0, st>>>(t1, t1f, o, v, vp);
+    eps_ff_kernel<<<(vp + 255) / 256, 256, 0, st>>>(eps_v, evf, v, vp);
     return cudaGetLastError();
 }
 

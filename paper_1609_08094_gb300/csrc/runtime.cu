@@ -206,8 +206,6 @@ static void build_operands_oz(Exec &ex, Problem &pb, const double *t2, const dou
     free_tmp(ex, tmp_oo, (size_t)o * o * o * v);
 }
 
-Dims make_dims(int o, int v) { return Dims{o, v, round_up(v, KPAD), round_up(o, KPAD), round_up(v, UPAD)}; }
-
 void build_operands(Exec &ex, Problem &pb, const double *t2, const double *vvvo, const double *ooov,
                     bool host) {
     if (ex.prec == TCORR_FP64_OZ) {
@@ -284,11 +282,12 @@ void build_epilogue_inputs(Exec &ex, Problem &pb, const double *eps_occ, const d
         const size_t vp = epi_vp(v);
         dalloc(ex, pb.t1, (size_t)o * vp * sizeof(float));
         dalloc(ex, pb.ovov, (size_t)o * o * vp * vp * sizeof(float));
+        dalloc(ex, pb.evf, vp * sizeof(float2));
         double *tmp1 = nullptr, *tmp2 = nullptr;
         const double *d1 = device_view(ex, t1, (size_t)o * v, host, tmp1);
         const double *d2 = device_view(ex, ovov, nov2, host, tmp2);
-        CK(launch_epilogue_f32_inputs(d1, d2, static_cast<float *>(pb.t1), static_cast<float *>(pb.ovov), o, v,
-                                      (int)vp, ex.stream));
+        CK(launch_epilogue_f32_inputs(d1, d2, pb.eps_v, static_cast<float *>(pb.t1), static_cast<float *>(pb.ovov),
+                                      pb.evf, o, v, (int)vp, ex.stream));
         free_tmp(ex, tmp1, (size_t)o * v);
         free_tmp(ex, tmp2, nov2);
     }
@@ -313,7 +312,7 @@ size_t problem_bytes(const Dims &d, int prec) {
     const size_t eb = elem_bytes(prec), parts = operand_planes(prec);
     size_t b = parts * eb * (o * v2 * d.dp + o * v2 * d.lp + o * o * v * d.dp + o * o * v * d.lp);
     const size_t ve = fp64_epilogue(prec) ? v : (size_t)epi_vp((int)v);  // FP32 inputs are padded
-    b += (o * o * ve * ve + o * ve) * u_elem_bytes(prec) + (o + v) * 8;
+    b += (o * o * ve * ve + o * ve) * u_elem_bytes(prec) + (o + v) * 8 + ve * 8;
     const size_t nb = (v + EPI_TE - 1) / EPI_TE;
     b += nb * (nb + 1) * (nb + 2) / 6 * 12;
     b += o * (o + 1) * (o + 2) / 6 * 28;
@@ -350,10 +349,11 @@ void fill_desc(Exec &ex, Problem &pb, int pbt) {
     d.eps_v = pb.eps_v;
     d.t1 = pb.t1;
     d.ovov = pb.ovov;
+    d.evf = pb.evf;
     d.tasks = pb.tasks;
     d.orbits = pb.orbits;
     d.task_e = pb.task_e;
-    pb.u_task = (int64_t)3 * pb.dm.v * pb.dm.v * pb.dm.vc;
+    pb.u_task = 3 * pb.dm.ug;
     if (ex.prec == TCORR_FP64) {
         pb.gemm_units = f64_units_per_task(pb.dm);
     } else if (ex.prec == TCORR_FP64_OZ) {
@@ -473,7 +473,7 @@ void launch_plan(Exec &ex, const Plan &pl, const Seg *d_segs, const SumSpan *d_s
         }
         {
             Timer tm(ex, KC_EPI);
-            CK(launch_epilogue(fp64_epilogue(ex.prec) ? TCORR_FP64 : ex.prec, w, st));
+            CK(launch_epilogue(fp64_epilogue(ex.prec) ? TCORR_FP64 : ex.prec, ex.sm_count, w, st));
             tm.stop();
         }
         {
@@ -543,7 +543,10 @@ void init_exec(Exec &ex, const tcorr_opts &op, void *stream) {
     if (ex.prec != TCORR_FP64 && !tc_supported(ex.cc_major, ex.cc_minor))
         throw Fail{TCORR_EUNSUPPORTED, "mixed precision needs the sm_103 tensor-core path (device is sm_" +
                                            std::to_string(ex.cc_major * 10 + ex.cc_minor) + ")"};
-    if (is_split(ex.prec)) CK(tc_prepare(ex.prec));  // kernel attributes, before any capture
+    if (is_split(ex.prec)) {  // kernel attributes, before any capture
+        CK(tc_prepare(ex.prec));
+        CK(epi_prepare());
+    }
     if (ex.prec == TCORR_FP64_OZ) CK(oz_prepare());
 }
 

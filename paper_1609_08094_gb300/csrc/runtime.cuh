@@ -37,13 +37,14 @@ struct Problem {
     Operands op;
     double *eps_o = nullptr, *eps_v = nullptr;  // FP64
     void *t1 = nullptr;      // FP64 or FP32 copy
-    void *ovov = nullptr;    // FP64 or FP32 copy [o][v][o][v]
+    void *ovov = nullptr;    // FP64 copy [o][v][o][v] or FP32 blocks (see launch_epilogue_f32_inputs)
+    float2 *evf = nullptr;   // mixed paths: eps_v as float-float pairs
     int64_t ntask = 0;
     int *tasks = nullptr;      // device [ntask][3]
     double *task_e = nullptr;  // device [ntask][2] (E4, E5 share)
     int norb = 0;              // epilogue block orbits per task
     int *orbits = nullptr;     // device [norb][3]
-    int64_t u_task = 0;        // U elements per task: 3 v v vc
+    int64_t u_task = 0;        // U elements per task: 3 ug
     unsigned long long *oz_max = nullptr;  // FP64 emulation: device [3] max |vvvo|, |t2|, |ooov| (bit patterns)
     int *oz_e = nullptr;                   // FP64 emulation: device [2] scale exponents
     int64_t gemm_units = 0;    // W-contraction work units per task
@@ -170,7 +171,6 @@ bool is_split(int prec);     // TF32x3 / BF16x3 (hi + lo operands, FP32 U and ep
 bool fp64_epilogue(int prec);  // FP64 and FP64 emulation: FP64 U, epilogue inputs and epilogue
 size_t elem_bytes(int prec);
 size_t u_elem_bytes(int prec);
-Dims make_dims(int o, int v);
 void build_operands(Exec &ex, Problem &pb, const double *t2, const double *vvvo, const double *ooov,
                     bool host);
 void build_epilogue_inputs(Exec &ex, Problem &pb, const double *eps_occ, const double *eps_vir,

@@ -388,7 +388,7 @@ tcorr_status tcorr_server_submit(tcorr_server_t s, const tcorr_problem *p, int64
     }
     const Dims dm = make_dims(p->o, p->v);
     const size_t fp = job_footprint(dm, s->ex.prec);
-    const int64_t u_task = (int64_t)3 * dm.v * dm.v * dm.vc;
+    const int64_t u_task = 3 * dm.ug;
     const int64_t norb = epilogue_orbits(dm.v);
     if (fp > s->budget || u_task > s->ex.u_cap || norb * 2 > s->ex.part_cap) {
         s->ex.last_error = "job footprint " + std::to_string(fp) + " bytes or one task's scratch exceeds the server's";

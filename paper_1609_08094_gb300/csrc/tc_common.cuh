@@ -456,5 +456,50 @@ inline bool encode(CUtensorMap *m, CUtensorMapDataType dt, int rank, void *base,
 }
 
 
+// Stores one thread's U row (fixed b < v, c < v of group g; a = a0 + j for
+// j < na, a0 a multiple of 8) into the mixed paths' cube layout
+// (tcorr_internal.cuh): group 0 at C0[a][b][c], 1 at C1[b][a][c], 2 at
+// C2[b][c][a].  Ut: the task's U block; nb: cubes per edge.  Every 8 values of
+// a lie in one cube; the swizzle is linear, so an element's offset in its
+// cube is the thread's part XOR the part of a & 7.  In every group the 8
+// values of c & 7 at fixed (a, b) fill one aligned 32-byte row, so a warp's
+// store (2 values of b x 16 of c) writes 4 whole sectors.
+__device__ __forceinline__ void store_u_cubes(float *Ut, int nb, int g, int a0, int b, int c, int na,
+                                              const float (&total)[128]) {
+    const int A0 = a0 >> 3, B = b >> 3, C = c >> 3, lb = b & 7, lc = c & 7;
+    int64_t base, step;
+    int offs[8];
+    if (g == 0) {
+        base = (((int64_t)A0 * nb + B) * nb + C) * 3 * 512;
+        step = (int64_t)nb * nb * 3 * 512;
+#pragma unroll
+        for (int q = 0; q < 8; q++) offs[q] = ucube_off(0, lb, lc) ^ ucube_off(q, 0, 0);
+    } else if (g == 1) {
+        base = ((((int64_t)B * nb + A0) * nb + C) * 3 + 1) * 512;
+        step = (int64_t)nb * 3 * 512;
+#pragma unroll
+        for (int q = 0; q < 8; q++) offs[q] = ucube_off(lb, 0, lc) ^ ucube_off(0, q, 0);
+    } else {  // element (x, y, z) = (b, c, a) of C2 at ucube_off(x, z, y)
+        base = ((((int64_t)B * nb + C) * nb + A0) * 3 + 2) * 512;
+        step = 3 * 512;
+#pragma unroll
+        for (int q = 0; q < 8; q++) offs[q] = ucube_off(lb, 0, lc) ^ ucube_off(0, q, 0);
+    }
+    float *p = Ut + base;
+    if (na >= 128) {
+#pragma unroll
+        for (int j = 0; j < 128; j++) {
+            p[offs[j & 7]] = total[j];
+            if ((j & 7) == 7) p += step;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 128; j++) {
+            if (j < na) p[offs[j & 7]] = total[j];
+            if ((j & 7) == 7) p += step;
+        }
+    }
+}
+
 }  // namespace tcx
 }  // namespace tcorr

@@ -123,7 +123,7 @@ tcorr_status tcorr_create(tcorr_t *out, int o, int v, const double *eps_occ,
         init_exec(ex, op, stream);
         const Dims dm = make_dims(o, v);
         const int64_t ntask = (int64_t)o * (o + 1) * (o + 2) / 6;
-        const int64_t u_task = (int64_t)3 * v * v * dm.vc;
+        const int64_t u_task = 3 * dm.ug;
         const size_t u_task_bytes = (size_t)u_task * u_elem_bytes(ex.prec);
         size_t free_b = 0, total_b = 0;
         CK(cudaMemGetInfo(&free_b, &total_b));
@@ -305,7 +305,7 @@ tcorr_status tcorr_batch_create(tcorr_batch_t *out, int n, const tcorr_problem *
             const Dims dm = make_dims(problems[m].o, problems[m].v);
             need += problem_bytes(dm, ex.prec);
             if (op.host_inputs) stage = std::max(stage, host_staging_bytes(dm));
-            u_task_max = std::max<int64_t>(u_task_max, (int64_t)3 * dm.v * dm.v * dm.vc);
+            u_task_max = std::max<int64_t>(u_task_max, 3 * dm.ug);
             norb_max = std::max<int64_t>(norb_max, epilogue_orbits(dm.v));
         }
         // 2 GiB of U per wave: fewer wave boundaries (each drains the GEMM and the
@@ -318,7 +318,7 @@ tcorr_status tcorr_batch_create(tcorr_batch_t *out, int n, const tcorr_problem *
         int64_t u_task_min = u_task_max;
         for (int m = 0; m < n; m++) {
             const Dims dm = make_dims(problems[m].o, problems[m].v);
-            u_task_min = std::min<int64_t>(u_task_min, (int64_t)3 * dm.v * dm.v * dm.vc);
+            u_task_min = std::min<int64_t>(u_task_min, 3 * dm.ug);
         }
         const int64_t max_wave_tasks = std::min<int64_t>(ex.wave_tasks, ex.u_cap / u_task_min + 1);
         ex.part_cap = std::max<int64_t>(norb_max * 2, max_wave_tasks * norb_max * 2);

@@ -29,10 +29,26 @@ enum { DERR_TIMEOUT_FULL = 1, DERR_TIMEOUT_EMPTY = 2, DERR_TIMEOUT_TMEM = 4, DER
 
 struct Dims {
     int o, v;
-    int dp;   // padded d extent (K of the vvvo segments)
-    int lp;   // padded l extent (K of the ooov segments)
-    int vc;   // padded c extent of U
+    int dp;      // padded d extent (K of the vvvo segments)
+    int lp;      // padded l extent (K of the ooov segments)
+    int vc;      // padded c extent of U (FP64 layouts)
+    int64_t ug;  // U elements per group tensor: room for either layout below
 };
+constexpr int UCUBE = 8;  // edge of the U cubes of the mixed paths (and of the epilogue's block orbits)
+__host__ __device__ inline Dims make_dims(int o, int v) {
+    const int vc = round_up(v, UPAD);
+    const int64_t vp = round_up(v, UCUBE);
+    const int64_t flat = (int64_t)v * v * vc, cubes = vp * vp * vp;
+    return Dims{o, v, round_up(v, KPAD), round_up(o, KPAD), vc, flat > cubes ? flat : cubes};
+}
+// Offset of element (x, y, z) (each < 8) inside a U cube of the mixed paths.
+// An XOR swizzle, linear over GF(2) in the bits of x, y, z, so that the six
+// ways the epilogue walks a cube (a warp holds 4 consecutive values of one
+// index and all 8 of another, the third fixed, in any assignment to x, y, z)
+// each touch 32 distinct shared-memory banks.
+__host__ __device__ inline int ucube_off(int x, int y, int z) {
+    return (x << 6) | ((y ^ (x & 3)) << 3) | (z ^ y ^ (x & 4));
+}
 
 // Operand layouts built by the prep kernels (element type T = double, float
 // (TF32 container) or __nv_bfloat16):
@@ -47,11 +63,19 @@ struct Dims {
 //                      + sum_l AoN[q][s][a][l] T2K[p][b][c][l]
 //                      + sum_l AoN[p][s][a][l] T2K[q][c][b][l]
 // and W^{abc}_{ijk} = U^{i;j,k}[a][b][c] + U^{j;i,k}[b][a][c] + U^{k;i,j}[c][a][b].
-// Storage of the three group tensors in the U scratch ([ntb][3][v][v][vc]):
-//   FP64 path: each U^g in its own [a][b][c] order (read transposed by the
-//   FP64 epilogue);  mixed paths: slots 0 and 2 in their own [a][b][c] order,
-//   slot 1 transposed to [b][a][c], so that W[x][y][z] = S0[x][y][z] +
-//   S1[x][y][z] + S2[z][x][y] (S = stored slot).
+// Storage of the three group tensors in the U scratch (3 ug elements per task):
+//   FP64 paths: each U^g as [a][b][c] with rows of vc (read transposed by the
+//   FP64 epilogue);
+//   mixed paths: each group as its term of W in W's own index order,
+//   C0[a][b][c] = U^0[a][b][c], C1[b][a][c] = U^1[a][b][c], C2[b][c][a] =
+//   U^2[a][b][c], so that W[x][y][z] = C0[x][y][z] + C1[x][y][z] +
+//   C2[x][y][z]; as cubes of 8^3 (nb = ceil(v / 8) per edge) with the three
+//   groups interleaved: cube (X, Y, Z) of group g at (((X nb + Y) nb + Z) 3
+//   + g) * 512 in the task's block, element (x, y, z) of it at
+//   ucube_off(x, y, z) in C0 and C1 and at ucube_off(x, z, y) in C2 (so that
+//   the contraction's stores, 8 consecutive c at fixed a and b, fill one
+//   32-byte sector in every group).  An epilogue block orbit reads the three
+//   terms of one W cube as one contiguous 6 KB copy.
 struct Operands {
     void *G = nullptr, *T2K = nullptr, *T2R = nullptr, *AoN = nullptr;       // FP64 or hi part
     void *Glo = nullptr, *T2Klo = nullptr, *T2Rlo = nullptr, *AoNlo = nullptr;  // lo part (mixed)
@@ -75,6 +99,7 @@ struct InstDesc {
     const void *G, *T2K, *T2R, *AoN;  // FP64 operand layouts (FP64 W contractions)
     const double *eps_o, *eps_v;
     const void *t1, *ovov;    // FP64 or FP32 copies for the epilogue
+    const float2 *evf;        // mixed epilogue: eps_v as float-float (hi, lo), zero padded to 8 nb
     const int *tasks;         // [ntask][3]
     const int *orbits;        // [norb][3]
     double *task_e;           // [ntask][2]
@@ -88,7 +113,7 @@ struct Seg {
     int inst;                 // index into the InstDesc array
     int ntb;                  // tasks in the segment
     int64_t task0;            // first task of the segment in the instance's list
-    int64_t u_off;            // element offset of the segment's U block: [ntb][3][v][v][vc]
+    int64_t u_off;            // element offset of the segment's U block: [ntb][3 ug]
     int64_t gemm0;            // prefix of W-contraction work units
     int64_t epi0;             // prefix of epilogue items (task, block orbit)
     int64_t red0;             // prefix of tasks
@@ -126,10 +151,11 @@ cudaError_t launch_transpose_pad(int kind, const double *in, void *out_hi, void 
                                  int64_t B, int R, int Rp, int64_t C,
                                  int64_t sb, int64_t sr, int64_t sc,
                                  int64_t ob, int64_t oc, double scale, cudaStream_t st);
-// out[n] = (float) in[n]
-// FP32 epilogue inputs: t1 as [o][vp] and (p x | q z) as slabs [p][q][x][z] with x, z < vp, zero padded
-cudaError_t launch_epilogue_f32_inputs(const double *t1, const double *ovov, float *t1f, float *ovf, int o,
-                                       int v, int vp, cudaStream_t st);
+// FP32 epilogue inputs, zero padded to vp = 8 nb: t1 as rows [o][vp]; (p x | q z)
+// as [p][q][X][Z][8][8] (8x8 blocks of x, z, each 256 contiguous bytes); eps_v
+// as float-float pairs [vp]
+cudaError_t launch_epilogue_f32_inputs(const double *t1, const double *ovov, const double *eps_v, float *t1f,
+                                       float *ovf, float2 *evf, int o, int v, int vp, cudaStream_t st);
 // tasks[n] = (i, j, k): the sorted occupied triples i <= j <= k of o orbitals
 // in lexicographic order; orbits[n] = (A, B, C): the sorted block triples
 // A <= B <= C of nb virtual blocks, lexicographic
@@ -141,7 +167,10 @@ int64_t f64_units_per_task(const Dims &dm);
 cudaError_t launch_ugemm_f64(const Wave &w, cudaStream_t st);
 
 // ---- epilogue.cu ---------------------------------------------------------
-cudaError_t launch_epilogue(int prec, const Wave &w, cudaStream_t st);
+// sm_count: persistent CTAs of the mixed epilogue (2 per SM); unused by FP64
+cudaError_t launch_epilogue(int prec, int sm_count, const Wave &w, cudaStream_t st);
+// sets the mixed epilogue's shared-memory attribute once per process (before any capture)
+cudaError_t epi_prepare();
 cudaError_t launch_task_reduce(const Wave &w, cudaStream_t st);
 // One range of one problem's task energies, summed (Kahan) into out[0..2] =
 // (E4, E5, E4 + E5) by launch_span_sums (one CTA per span).
