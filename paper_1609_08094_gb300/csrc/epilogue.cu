@@ -372,11 +372,21 @@ constexpr int EPI_CTAS = EPI_F32_CTAS;          // CTAs per SM
 struct EpiStage {
     float cube[6][3][512];       // [slot][group]: the three terms of the slot's W cube (as stored in U)
     float ov[3][3][3][F8 * F8];  // [(j y|k z), (i x|k z), (i x|j y)][block][block][8x8]
+    float ov_pad[F8 * F8];       // the fourth row of the last 4-row gather
     float t1[3][3][F8];          // [occupied i, j, k][orbit block][local]
+    float t1_pad[3][F8];
     float2 ev[3][F8];            // [orbit block][local] eps_v as float-float (hi, lo)
+    float2 ev_pad[F8];
 };
-static_assert(sizeof(EpiStage) % 16 == 0, "stages keep 16-byte alignment");
-constexpr size_t EPI_SMEM = EPI_STAGES * sizeof(EpiStage);
+// each 4-row gather lands 128-byte aligned, rows back to back
+static_assert(offsetof(EpiStage, ov) % 128 == 0 && offsetof(EpiStage, t1) % 128 == 0 &&
+                  offsetof(EpiStage, ev) % 128 == 0 && sizeof(EpiStage) % 128 == 0,
+              "gather destinations are 128-byte aligned");
+static_assert(offsetof(EpiStage, ov_pad) == offsetof(EpiStage, ov) + 27 * 256 &&
+                  offsetof(EpiStage, t1_pad) == offsetof(EpiStage, t1) + 9 * 32 &&
+                  offsetof(EpiStage, ev_pad) == offsetof(EpiStage, ev) + 3 * 64,
+              "gather rows are contiguous");
+constexpr size_t EPI_SMEM = EPI_STAGES * sizeof(EpiStage) + 128;  // + alignment slack
 
 struct EpiMeta {
     double *out;                 // the orbit's (E4, E5) partial
@@ -386,6 +396,16 @@ struct EpiMeta {
     int kind;                    // 0: no more orbits, 1: three distinct blocks, 2: repeated blocks
     int v;                       // virtual orbitals of the problem
 };
+
+// Four rows r0..r3 of a 2-D tensor map (box: one row) to dst, back to back.
+__device__ __forceinline__ void gather4_load(uint32_t dst, const CUtensorMap *map, uint32_t bar, int r0, int r1,
+                                             int r2, int r3) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(dst),
+        "l"(map), "r"(bar), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3)
+        : "memory");
+}
 
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
     asm volatile(
@@ -397,7 +417,7 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
 __global__ void __launch_bounds__(EPI_THREADS, EPI_CTAS) epilogue_f32_kernel(const __grid_constant__ Wave wv) {
     using namespace tcx;
     extern __shared__ __align__(128) unsigned char epi_smem[];
-    EpiStage *stg = reinterpret_cast<EpiStage *>(epi_smem);
+    EpiStage *stg = reinterpret_cast<EpiStage *>(epi_smem + (((smem_u32(epi_smem) + 127u) & ~127u) - smem_u32(epi_smem)));
     __shared__ EpiMeta meta[EPI_STAGES];
     __shared__ __align__(8) uint64_t bar_full[EPI_STAGES], bar_empty[EPI_STAGES];
     __shared__ __align__(8) uint64_t bar_rfull[2], bar_rempty[2];
@@ -442,8 +462,8 @@ __global__ void __launch_bounds__(EPI_THREADS, EPI_CTAS) epilogue_f32_kernel(con
         int64_t ug = 0;
         const int *tasks = nullptr, *orbits = nullptr;
         const double *eps_o = nullptr;
-        const float *Useg = nullptr, *ovf = nullptr, *t1f = nullptr;
-        const float2 *evf = nullptr;
+        const float *Useg = nullptr;
+        const CUtensorMap *emaps = nullptr;
         int ti = 0, tj = 0, tkk = 0;
         ff eijk = {0.f, 0.f};
         int pf_orb = -1, pf0 = 0, pf1 = 0, pf2 = 0;  // prefetched orbit triple (current segment)
@@ -465,9 +485,7 @@ __global__ void __launch_bounds__(EPI_THREADS, EPI_CTAS) epilogue_f32_kernel(con
                 tasks = p.tasks;
                 orbits = p.orbits;
                 Useg = static_cast<const float *>(wv.U) + sg.u_off;
-                ovf = static_cast<const float *>(p.ovov);
-                t1f = static_cast<const float *>(p.t1);
-                evf = p.evf;
+                emaps = p.emaps;
                 eps_o = p.eps_o;
                 tb_c = -1;
                 pf_orb = -1;
@@ -526,12 +544,13 @@ __global__ void __launch_bounds__(EPI_THREADS, EPI_CTAS) epilogue_f32_kernel(con
                 if (smap[s] == s) { loaded |= 1 << s; nload++; }
             }
             const uint32_t full = smem_u32(&bar_full[stage]);
-            // the copies of an orbit: e in [0, 6) the U cubes of slot e (the three
-            // group terms, 6 KB); [6, 33) the 27 ovov sub-blocks (256 B);
-            // [33, 42) the 9 t1 rows (32 B); [42, 45) the 3 energy blocks (64 B).
-            // Two producer warps: warp 0 takes the cubes, t1 and energies (and
-            // writes the stage's meta), warp 1 the ovov sub-blocks.
-            constexpr uint32_t ov_bytes = 27 * 256, te_bytes = 9 * 32 + 3 * 64;
+            // the copies of an orbit: the U cubes of each distinct slot (the three
+            // group terms side by side, one 6 KB bulk copy each); the 27 ovov
+            // sub-blocks, the 9 t1 rows and the 3 energy blocks as 4-row gathers
+            // of their row maps (7, 3 and 1 gathers; a gather's spare rows repeat
+            // a valid one and land in the pad rows).  Warp 0 takes the cubes and
+            // the energies (and writes the stage's meta), warp 1 ovov and t1.
+            constexpr uint32_t ov_bytes = 7 * 4 * 256 + 3 * 4 * 32, ev_bytes = 4 * 64;
             const uint32_t u_bytes = (uint32_t)nload * 3 * 2048;
             if (lane == 0 && pw != 0) mbar_expect_tx(full, ov_bytes);
             if (lane == 0 && pw == 0) {
@@ -543,35 +562,43 @@ __global__ void __launch_bounds__(EPI_THREADS, EPI_CTAS) epilogue_f32_kernel(con
                 for (int s = 0; s < 6; s++) m.smap[s] = smap[s];
                 m.kind = (ob0 < ob1 && ob1 < ob2) ? 1 : 2;
                 m.v = v;
-                mbar_expect_tx(full, u_bytes + te_bytes + (EPI_PRODUCERS == 1 ? ov_bytes : 0u));
+                mbar_expect_tx(full, u_bytes + ev_bytes + (EPI_PRODUCERS == 1 ? ov_bytes : 0u));
             }
             __syncwarp();
             const float *Ut = Useg + (int64_t)tb * 3 * ug;
             const uint32_t sb = smem_u32(&stg[stage]);
-            const int ncopy = EPI_PRODUCERS == 1 ? 45 : (pw == 0 ? 18 : 27);
-            for (int k = lane; k < ncopy; k += 32) {
-                const int e = EPI_PRODUCERS == 1 ? k : (pw == 0 ? (k < 6 ? k : k + 27) : k + 6);
+            // e in [0, 6): cube of slot e; 6: energies; [7, 14): ovov gathers; [14, 17): t1 gathers
+            const int e = EPI_PRODUCERS == 1 ? lane : (pw == 0 ? lane : lane + 7);
+            if (lane < (EPI_PRODUCERS == 1 ? 17 : (pw == 0 ? 7 : 10))) {
                 if (e < 6) {
-                    if (!((loaded >> e) & 1)) continue;
-                    const int X = pick3(ob0, ob1, ob2, perm_pos(e, 0)), Y = pick3(ob0, ob1, ob2, perm_pos(e, 1)),
-                              Z = pick3(ob0, ob1, ob2, perm_pos(e, 2));
-                    bulk_load(sb + (uint32_t)offsetof(EpiStage, cube) + (uint32_t)e * 6144u,
-                              Ut + (((int64_t)X * nb + Y) * nb + Z) * 3 * 512, 6144u, full);
-                } else if (e < 33) {
-                    const int q = e - 6, sl = q / 9, ba = (q / 3) % 3, bc = q % 3;
-                    const int first = sl == 0 ? tj : ti, second = sl == 2 ? tj : tkk;
-                    const int X = pick3(ob0, ob1, ob2, ba), Z = pick3(ob0, ob1, ob2, bc);
-                    bulk_load(sb + (uint32_t)offsetof(EpiStage, ov) + (uint32_t)q * 256u,
-                              ovf + ((((int64_t)first * o + second) * nb + X) * nb + Z) * 64, 256u, full);
-                } else if (e < 42) {
-                    const int q = e - 33, oc = q / 3, b = q - 3 * oc;
-                    const int occ = oc == 0 ? ti : (oc == 1 ? tj : tkk);
-                    bulk_load(sb + (uint32_t)offsetof(EpiStage, t1) + (uint32_t)q * 32u,
-                              t1f + (int64_t)occ * nb * F8 + pick3(ob0, ob1, ob2, b) * F8, 32u, full);
+                    if ((loaded >> e) & 1) {
+                        const int X = pick3(ob0, ob1, ob2, perm_pos(e, 0)), Y = pick3(ob0, ob1, ob2, perm_pos(e, 1)),
+                                  Z = pick3(ob0, ob1, ob2, perm_pos(e, 2));
+                        bulk_load(sb + (uint32_t)offsetof(EpiStage, cube) + (uint32_t)e * 6144u,
+                                  Ut + (((int64_t)X * nb + Y) * nb + Z) * 3 * 512, 6144u, full);
+                    }
+                } else if (e == 6) {
+                    gather4_load(sb + (uint32_t)offsetof(EpiStage, ev), emaps + 2, full, ob0, ob1, ob2, ob0);
+                } else if (e < 14) {
+                    // rows ((p o + q) nb + X) nb + Z of the sub-blocks q = 4 k .. 4 k + 3
+                    int r[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int q = min(4 * (e - 7) + u, 26), sl = q / 9, ba = (q / 3) % 3, bc = q % 3;
+                        const int first = sl == 0 ? tj : ti, second = sl == 2 ? tj : tkk;
+                        r[u] = ((first * o + second) * nb + pick3(ob0, ob1, ob2, ba)) * nb + pick3(ob0, ob1, ob2, bc);
+                    }
+                    gather4_load(sb + (uint32_t)offsetof(EpiStage, ov) + (uint32_t)(e - 7) * 1024u, emaps + 0, full,
+                                 r[0], r[1], r[2], r[3]);
                 } else {
-                    const int b = e - 42;
-                    bulk_load(sb + (uint32_t)offsetof(EpiStage, ev) + (uint32_t)b * 64u,
-                              evf + pick3(ob0, ob1, ob2, b) * F8, 64u, full);
+                    int r[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int q = min(4 * (e - 14) + u, 8), oc = q / 3, b = q - 3 * oc;
+                        r[u] = (oc == 0 ? ti : (oc == 1 ? tj : tkk)) * nb + pick3(ob0, ob1, ob2, b);
+                    }
+                    gather4_load(sb + (uint32_t)offsetof(EpiStage, t1) + (uint32_t)(e - 14) * 128u, emaps + 1, full,
+                                 r[0], r[1], r[2], r[3]);
                 }
             }
             n++;
@@ -818,6 +845,36 @@ __global__ void __launch_bounds__(NT) span_sum_kernel(const SumSpan *spans) {
 int epilogue_orbits(int v) {
     const int nb = (v + 7) / 8;
     return nb * (nb + 1) * (nb + 2) / 6;
+}
+
+cudaError_t epi_fill_desc(InstDesc &d, std::string &err) {
+    const uint64_t o = (uint64_t)d.dm.o, nb = (uint64_t)(d.dm.v + F8 - 1) / F8;
+    if (!d.ovov || !d.t1 || !d.evf) {
+        err = "mixed epilogue inputs missing";
+        return cudaErrorInvalidValue;
+    }
+    if (o * o * nb * nb >= ((uint64_t)1 << 31)) {  // gather rows are 32-bit coordinates
+        err = "o, v beyond the mixed epilogue's row range";
+        return cudaErrorInvalidValue;
+    }
+    // row maps for 4-row gathers (box: one row, no swizzle): ovov 8x8 blocks
+    // [p][q][X][Z] as rows of 64 floats, t1 as rows [p][X] of 8, eps_v (hi, lo)
+    // as rows [X] of 16 floats
+    struct M {
+        void *base;
+        uint64_t cols, rows;
+        const char *what;
+    } ms[3] = {{const_cast<void *>(d.ovov), 64, o * o * nb * nb, "ovov blocks"},
+               {const_cast<void *>(d.t1), 8, o * nb, "t1 rows"},
+               {const_cast<float2 *>(d.evf), 16, nb, "eps_v blocks"}};
+    for (int k = 0; k < 3; k++) {
+        const uint64_t dims[2] = {ms[k].cols, ms[k].rows}, strides[1] = {ms[k].cols * 4};
+        const uint32_t box[2] = {(uint32_t)ms[k].cols, 1};
+        if (!tcx::encode(&d.emaps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ms[k].base, dims, strides, box, err,
+                         ms[k].what, CU_TENSOR_MAP_SWIZZLE_NONE))
+            return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t epi_prepare() {

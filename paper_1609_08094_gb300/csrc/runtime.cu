@@ -364,6 +364,7 @@ void fill_desc(Exec &ex, Problem &pb, int pbt) {
         std::string msg;
         if (tc_fill_desc(d, operand_prec(ex.prec, pb.dm.o, pb.dm.v), pb.op, pbt, TC_KB, ex.pair, msg) != cudaSuccess)
             throw Fail{TCORR_EUNSUPPORTED, msg};
+        if (epi_fill_desc(d, msg) != cudaSuccess) throw Fail{TCORR_EUNSUPPORTED, msg};
         pb.gemm_units = tc_units_per_task(d);
     }
 }

@@ -437,7 +437,8 @@ inline PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 inline bool encode(CUtensorMap *m, CUtensorMapDataType dt, int rank, void *base, const uint64_t *dims,
-            const uint64_t *strides_bytes, const uint32_t *box, std::string &err, const char *what) {
+            const uint64_t *strides_bytes, const uint32_t *box, std::string &err, const char *what,
+            CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_64B) {
     auto fn = get_encode();
     if (!fn) {
         err = "cuTensorMapEncodeTiled unavailable";
@@ -446,7 +447,7 @@ inline bool encode(CUtensorMap *m, CUtensorMapDataType dt, int rank, void *base,
     uint32_t es[5] = {1, 1, 1, 1, 1};
     CUresult r = fn(m, dt, (cuuint32_t)rank, base, (const cuuint64_t *)dims, (const cuuint64_t *)strides_bytes,
                     (const cuuint32_t *)box, (const cuuint32_t *)es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         err = std::string("cuTensorMapEncodeTiled failed for ") + what + " (CUresult " + std::to_string((int)r) + ")";

@@ -87,6 +87,7 @@ struct Operands {
 // maps (alignof(CUtensorMap)), so an array of them keeps every map aligned.
 struct InstDesc {
     CUtensorMap maps[6][2];   // tensor-core operand maps [G, G swapped, T2K, T2K swapped, T2R, AoN][hi, lo]
+    CUtensorMap emaps[3];     // mixed epilogue row maps for 4-row gathers: ovov 8x8 blocks, t1 rows, eps_v blocks
     Dims dm;
     int pb, pc;               // tensor-core pair tile: pb values of b x pc values of c (pb * pc = 128)
     int kb;                   // K chunks per tensor-core accumulator block
@@ -171,6 +172,8 @@ cudaError_t launch_ugemm_f64(const Wave &w, cudaStream_t st);
 cudaError_t launch_epilogue(int prec, int sm_count, const Wave &w, cudaStream_t st);
 // sets the mixed epilogue's shared-memory attribute once per process (before any capture)
 cudaError_t epi_prepare();
+// encodes d.emaps from d.ovov, d.t1, d.evf (the FP32 epilogue inputs) and d.dm
+cudaError_t epi_fill_desc(InstDesc &d, std::string &err);
 cudaError_t launch_task_reduce(const Wave &w, cudaStream_t st);
 // One range of one problem's task energies, summed (Kahan) into out[0..2] =
 // (E4, E5, E4 + E5) by launch_span_sums (one CTA per span).
