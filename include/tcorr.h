@@ -64,8 +64,11 @@ typedef enum {
     TCORR_FP64_OZ = 3  /* FP64-accurate W contractions on the BF16 tensor cores: each operand split
                           into 5 signed 7-bit slices under one power-of-two scale per operand side
                           (Ozaki scheme), slice products summed exactly in FP32 per 32-element K
-                          chunk and in int64 across chunks, U rounded once to FP64; FP64 energy
-                          epilogue.  sm_103 only; device or host inputs; batch and server too */
+                          chunk and in int64 across chunks, U rounded once to FP64 and stored as
+                          a float-float (hi, lo) pair (~48 significant bits); the energy epilogue
+                          in float-float arithmetic on the FP32 pipe (relative error ~2^-44 per
+                          operation) with FP64 sums from the orbit on.  sm_103 only; device or
+                          host inputs; batch and server too */
 } tcorr_precision;
 
 /* TCORR_BF16X3 problems below this many algorithmic flops run on TF32 operands */

@@ -91,6 +91,40 @@ __device__ __forceinline__ ff ff_of(double x) {  // x rounded to ~48 bits
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
+// A float-float number with arithmetic operators, the compute type of the
+// FP64-emulation epilogue: W, t1, ovov and the orbital energies arrive as
+// (hi, lo) pairs, so the epilogue runs on the FP32 pipe (64x GB300's FP64
+// rate).  Sums as ff_add; products a.hi b.hi exactly (FMA residual) plus the
+// cross terms a.hi b.lo + a.lo b.hi; quotients as a product with ff_recip.
+// Relative error per operation about 2^-44 of the operands' magnitudes.
+struct dd {
+    float hi, lo;
+    dd() = default;
+    __device__ __forceinline__ explicit dd(int c) : hi((float)c), lo(0.f) {}  // small integers: exact
+    __device__ __forceinline__ explicit dd(double x) {
+        hi = (float)x;
+        lo = (float)(x - (double)hi);
+    }
+    __device__ __forceinline__ dd(ff a) : hi(a.hi), lo(a.lo) {}
+    __device__ __forceinline__ operator ff() const { return ff{hi, lo}; }
+    __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+    __device__ __forceinline__ dd &operator+=(dd b) { return *this = dd(ff_add(*this, b)); }
+};
+__device__ __forceinline__ dd operator+(dd a, dd b) { return dd(ff_add(a, b)); }
+__device__ __forceinline__ dd operator-(dd a, dd b) { return dd(ff_sub(a, b)); }
+__device__ __forceinline__ dd operator*(dd a, dd b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return dd(ff_fast(p, e));
+}
+__device__ __forceinline__ dd operator/(dd a, dd b) { return a * dd(ff_recip(b)); }
+// a U value of the FP64-emulation path: (hi, lo) floats in the 8 bytes of a double
+__device__ __forceinline__ dd dd_bits(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return dd(ff{__int_as_float((int)(unsigned)u), __int_as_float((int)(unsigned)(u >> 32))});
+}
+
 // Sum over the CTA of one (E4, E5) pair per thread, in a fixed order, into
 // out[0..1]: the NT pairs through shared memory, NT / 32 per lane of warp 0,
 // then a shuffle tree.  (A shuffle tree over all NT threads would put ten
@@ -117,11 +151,25 @@ __device__ __forceinline__ void cta_sum2(double a4, double a5, double (*red)[2],
     }
 }
 
+// A U value as the compute type: FP64 as is, or the (hi, lo) pair of the
+// FP64-emulation path; and the virtual orbital energy x in the compute type
+template <typename CT> __device__ __forceinline__ CT u_val(double bits);
+template <> __device__ __forceinline__ double u_val<double>(double bits) { return bits; }
+template <> __device__ __forceinline__ dd u_val<dd>(double bits) { return dd_bits(bits); }
+template <typename CT> __device__ __forceinline__ CT eps_vir(const InstDesc &p, int x);
+template <> __device__ __forceinline__ double eps_vir<double>(const InstDesc &p, int x) { return p.eps_v[x]; }
+template <> __device__ __forceinline__ dd eps_vir<dd>(const InstDesc &p, int x) {
+    const float2 e = p.evf[x];
+    return dd(ff{e.x, e.y});
+}
+
 // FP64 epilogue; TE: cube edge.  Orbits of three distinct blocks take the
 // element-orbit form (the six orderings of one (a,b,c) share one denominator
 // and the E/O expansion of Z, as in the mixed epilogue), orbits with repeated
-// blocks the generic per-element form.
-template <typename UT, typename CT, int TE>
+// blocks the generic per-element form.  CT = double (FP64 path: U, t1, ovov
+// in FP64) or dd (FP64 emulation: all of them float-float pairs, so that no
+// operation per element runs on the FP64 pipe).
+template <typename CT, int TE>
 __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT *Ws = reinterpret_cast<CT *>(smem_raw);
@@ -149,10 +197,10 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
     // below are issued before any barrier
     const int ob0 = p.orbits[3 * orb], ob1 = p.orbits[3 * orb + 1], ob2 = p.orbits[3 * orb + 2];
 #define OBP(s, d) pick3(ob0, ob1, ob2, perm_pos((s), (d)))
-    const UT *U0 = static_cast<const UT *>(wv.U) + sg.u_off + (int64_t)(tb * 3 + 0) * p.dm.ug;
-    const UT *U1 = U0 + p.dm.ug;
-    const UT *U2 = U1 + p.dm.ug;
-    static_assert(sizeof(UT) == 8 && TE == 8, "16-byte loads of 8-element FP64 rows");
+    const double *U0 = static_cast<const double *>(wv.U) + sg.u_off + (int64_t)(tb * 3 + 0) * p.dm.ug;
+    const double *U1 = U0 + p.dm.ug;
+    const double *U2 = U1 + p.dm.ug;
+    static_assert(sizeof(CT) == 8 && TE == 8, "16-byte loads of 8-element rows of 8-byte values");
     // pass A loads: W = U0[x][y][z] + U1[y][x][z] (z fastest, pairs of z); pass B
     // loads: U2[z][x][y] (y fastest, pairs of y).  A row never ends within a
     // pair (rows are padded to 16), so a pair that starts inside [0, v) is in bounds.
@@ -196,8 +244,8 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
         const int l0 = l / (TE * TE), l1 = (l / TE) % TE, l2 = l % TE;
         const int z = OBP(s, 2) * TE + l2;
         CT *wp = Ws + s * CUBE + (l0 * TE + l1) * TP + l2;
-        wp[0] = (z < v) ? CT(ra[it].x) + CT(rb[it].x) : CT(0);     // row padding is not data
-        wp[1] = (z + 1 < v) ? CT(ra[it].y) + CT(rb[it].y) : CT(0);
+        wp[0] = (z < v) ? u_val<CT>(ra[it].x) + u_val<CT>(rb[it].x) : CT(0);  // row padding is not data
+        wp[1] = (z + 1 < v) ? u_val<CT>(ra[it].y) + u_val<CT>(rb[it].y) : CT(0);
     }
     __syncthreads();
 #pragma unroll
@@ -207,14 +255,14 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
         const int m2 = l / (TE * TE), m0 = (l / TE) % TE, m1 = l % TE;
         const int yb = OBP(s, 1) * TE + m1;
         CT *wp = Ws + s * CUBE + (m0 * TE + m1) * TP + m2;
-        if (yb < v) wp[0] += CT(rc[it].x);
-        if (yb + 1 < v) wp[TP] += CT(rc[it].y);
+        if (yb < v) wp[0] += u_val<CT>(rc[it].x);
+        if (yb + 1 < v) wp[TP] += u_val<CT>(rc[it].y);
     }
     __syncthreads();
 
     const CT *t1 = static_cast<const CT *>(p.t1);
     const CT *ov = static_cast<const CT *>(p.ovov);
-    const double eijk = p.eps_o[ti] + p.eps_o[tj] + p.eps_o[tkk];
+    const CT eijk = CT(p.eps_o[ti] + p.eps_o[tj] + p.eps_o[tkk]);
     const CT coef[6] = {CT(8), CT(-4), CT(-4), CT(2), CT(2), CT(-4)};
     // ovov rows used by Y: (j y | k z), (i x | k z), (i x | j y)
     const CT *ov_jk = ov + ((int64_t)tj * v * o + tkk) * v;   // [y][z] stride o*v in y
@@ -241,7 +289,7 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
         const CT jk_bc = ov_jk[b * ovs + c], jk_cb = ov_jk[c * ovs + b];
         const CT ik_bc = ov_ik[b * ovs + c], ik_cb = ov_ik[c * ovs + b];
         const CT ij_bc = ov_ij[b * ovs + c], ij_cb = ov_ij[c * ovs + b];
-        const CT ebc = eijk - p.eps_v[b] - p.eps_v[c];
+        const CT ebc = eijk - eps_vir<CT>(p, b) - eps_vir<CT>(p, c);
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int la = la0 + h * (TE / 2), a = A0 + la;
@@ -272,7 +320,7 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
             const CT wy = w0 * y0 + w1 * y1 + w2 * y2 + w3 * y3 + w4 * y4 + w5 * y5;
             const CT q4 = CT(6) * ww + CT(2) * (E * E + O * O) - CT(8) * E * O;
             const CT q5 = CT(6) * wy + (CT(2) * E - CT(4) * O) * (y0 + y3 + y4) + (CT(2) * O - CT(4) * E) * (y1 + y2 + y5);
-            const CT r = CT(1) / (ebc - p.eps_v[a]);
+            const CT r = CT(1) / (ebc - eps_vir<CT>(p, a));
             a4 += q4 * r;
             a5 += q5 * r;
         }
@@ -299,7 +347,7 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
             const CT w0 = Ws[s * CUBE + (lv0 * TE + lv1) * TP + lv2];
             const CT yv = t1[ti * v + x] * ov_jk[y * ovs + z] + t1[tj * v + y] * ov_ik[x * ovs + z] +
                           t1[tkk * v + z] * ov_ij[x * ovs + y];
-            const CT dn = eijk - p.eps_v[x] - p.eps_v[y] - p.eps_v[z];
+            const CT dn = eijk - eps_vir<CT>(p, x) - eps_vir<CT>(p, y) - eps_vir<CT>(p, z);
             const CT r = CT(1) / dn;
             a4 += zv * w0 * r;
             a5 += zv * yv * r;
@@ -893,7 +941,12 @@ cudaError_t launch_epilogue(int prec, int sm_count, const Wave &w, cudaStream_t 
     if (w.n_epi > 0x7fffffff) return cudaErrorInvalidConfiguration;
     if (prec == TCORR_FP64) {
         const size_t smem = sizeof(double) * 6 * 8 * 8 * 9;
-        epilogue_kernel<double, double, 8><<<(unsigned)w.n_epi, NT, smem, st>>>(w);
+        epilogue_kernel<double, 8><<<(unsigned)w.n_epi, NT, smem, st>>>(w);
+        return cudaGetLastError();
+    }
+    if (prec == TCORR_FP64_OZ) {
+        const size_t smem = sizeof(dd) * 6 * 8 * 8 * 9;
+        epilogue_kernel<dd, 8><<<(unsigned)w.n_epi, NT, smem, st>>>(w);
         return cudaGetLastError();
     }
     cudaError_t e = epi_prepare();

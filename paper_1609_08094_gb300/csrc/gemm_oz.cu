@@ -41,6 +41,25 @@
 namespace tcorr {
 namespace {
 
+// t * 2^k as a float-float pair (hi, lo), hi + lo = t 2^k to about 2^-48
+// relative, with integer and FP32 operations only: t = t2 2^48 + t1 2^24 + t0
+// with |t2| < 2^15 and 0 <= t1, t0 < 2^24, each part exact in FP32; Knuth's
+// TwoSum of the two largest, then the smallest added (one rounding, of the
+// small parts only); the power-of-two scale is exact in the normal range.
+__device__ __forceinline__ float2 int64_to_ff(long long t, int k) {
+    const long long t2 = t >> 48;
+    const long long rem = t - (t2 << 48);
+    const float f2 = (float)(int)t2 * 0x1p48f, f1 = (float)(int)(rem >> 24) * 0x1p24f;
+    const float f0 = (float)(int)(rem & 0xffffff);
+    float s = f2 + f1, bb = s - f2;
+    float e = (f2 - (s - bb)) + (f1 - bb);  // s + e == f2 + f1
+    const float s2 = s + f0, b2 = s2 - s;
+    e += (s - (s2 - b2)) + (f0 - b2);       // s2 + e == t up to the rounding of e
+    const float hi = s2 + e, lo = e - (hi - s2);
+    return make_float2(ldexpf(hi, k), ldexpf(lo, k));
+}
+
+
 using namespace tcx;
 
 constexpr int OZ_S = 5;          // slices per operand
@@ -298,17 +317,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ugemm_oz_kernel(const __grid_co
                 if (lane == 0) fail(&abort_sh, wv.err, DERR_TIMEOUT_TMEM);
                 break;
             }
-            // U^g[a][b][c] in FP64 (the FP64 path's layout for every group)
+            // U^g[a][b][c] in the FP64 path's layout, each value as a float-float
+            // (hi, lo) pair in its 8 bytes (about 48 significant bits), so that the
+            // epilogue works on the FP32 pipe; formed from the exact int64 total
+            // without the FP64 pipe (int64_to_ff)
             const int b = w.bt * d.pb + lb, c = w.ct * d.pc + lc;
             if (b < v && c < v) {
-                const double scale = ldexp(1.0, d.oz_e[0] + d.oz_e[1] - OZ_BETA * (OZ_S + 1));
+                const int scale_exp = d.oz_e[0] + d.oz_e[1] - OZ_BETA * (OZ_S + 1);
                 const int a0 = w.n * OZ_N + half * OZ_HALF;
                 const int64_t stride = (int64_t)v * vc;
-                double *Ug = static_cast<double *>(wv.U) + u_seg + (int64_t)(w.tb * 3 + w.g) * d.dm.ug +
+                float2 *Ug = static_cast<float2 *>(wv.U) + u_seg + (int64_t)(w.tb * 3 + w.g) * d.dm.ug +
                              (int64_t)b * vc + c + (int64_t)a0 * stride;
 #pragma unroll
                 for (int j = 0; j < OZ_HALF; j++) {
-                    if (a0 + j < v) *Ug = (double)tot[j] * scale;
+                    if (a0 + j < v) *Ug = int64_to_ff(tot[j], scale_exp);
                     Ug += stride;
                 }
             }

@@ -101,6 +101,15 @@ __global__ void eps_ff_kernel(const double *__restrict__ e, float2 *__restrict__
     out[x] = make_float2(hi, static_cast<float>(d - static_cast<double>(hi)));
 }
 
+// FP64 values to float-float pairs in place (the same 8 bytes per value)
+__global__ void to_ff_kernel(double *__restrict__ x, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = x[i];
+        const float hi = static_cast<float>(d);
+        reinterpret_cast<float2 *>(x)[i] = make_float2(hi, static_cast<float>(d - static_cast<double>(hi)));
+    }
+}
+
 __global__ void pad_rows_kernel(const double *__restrict__ in, float *__restrict__ out, int rows, int v,
                                 int vp) {
     const int64_t n = (int64_t)rows * vp;
@@ -130,6 +139,15 @@ cudaError_t launch_transpose_pad(int kind, const double *in, void *out_hi, void 
     else
         transpose_pad_kernel<2><<<grid, blk, 0, st>>>(in, out_hi, out_lo, B, R, Rp, C, sb, sr, sc,
                                                       ob, oc, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_epilogue_ff_inputs(double *t1, double *ovov, const double *eps_v, float2 *evf, int o, int v,
+                                      cudaStream_t st) {
+    const int64_t n = (int64_t)o * v * o * v, blocks = (n + 255) / 256;
+    to_ff_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(ovov, n);
+    to_ff_kernel<<<(unsigned)(((int64_t)o * v + 255) / 256), 256, 0, st>>>(t1, (int64_t)o * v);
+    eps_ff_kernel<<<(v + 255) / 256, 256, 0, st>>>(eps_v, evf, v, v);
     return cudaGetLastError();
 }
 

@@ -278,6 +278,11 @@ void build_epilogue_inputs(Exec &ex, Problem &pb, const double *eps_occ, const d
         dalloc(ex, pb.ovov, nov2 * sizeof(double));
         CK(cudaMemcpyAsync(pb.t1, t1, (size_t)o * v * sizeof(double), kd, ex.stream));
         CK(cudaMemcpyAsync(pb.ovov, ovov, nov2 * sizeof(double), kd, ex.stream));
+        if (ex.prec == TCORR_FP64_OZ) {  // the emulation's epilogue works in float-float
+            dalloc(ex, pb.evf, (size_t)v * sizeof(float2));
+            CK(launch_epilogue_ff_inputs(static_cast<double *>(pb.t1), static_cast<double *>(pb.ovov), pb.eps_v,
+                                         pb.evf, o, v, ex.stream));
+        }
     } else {
         const size_t vp = epi_vp(v);
         dalloc(ex, pb.t1, (size_t)o * vp * sizeof(float));
@@ -474,7 +479,7 @@ void launch_plan(Exec &ex, const Plan &pl, const Seg *d_segs, const SumSpan *d_s
         }
         {
             Timer tm(ex, KC_EPI);
-            CK(launch_epilogue(fp64_epilogue(ex.prec) ? TCORR_FP64 : ex.prec, ex.sm_count, w, st));
+            CK(launch_epilogue(ex.prec, ex.sm_count, w, st));
             tm.stop();
         }
         {

@@ -38,7 +38,7 @@ struct Problem {
     double *eps_o = nullptr, *eps_v = nullptr;  // FP64
     void *t1 = nullptr;      // FP64 or FP32 copy
     void *ovov = nullptr;    // FP64 copy [o][v][o][v] or FP32 blocks (see launch_epilogue_f32_inputs)
-    float2 *evf = nullptr;   // mixed paths: eps_v as float-float pairs
+    float2 *evf = nullptr;   // mixed paths and FP64 emulation: eps_v as float-float pairs
     int64_t ntask = 0;
     int *tasks = nullptr;      // device [ntask][3]
     double *task_e = nullptr;  // device [ntask][2] (E4, E5 share)

@@ -99,8 +99,8 @@ struct InstDesc {
     const int *oz_e;          // FP64 emulation: device [2] scale exponents of the A and B operand sides
     const void *G, *T2K, *T2R, *AoN;  // FP64 operand layouts (FP64 W contractions)
     const double *eps_o, *eps_v;
-    const void *t1, *ovov;    // FP64 or FP32 copies for the epilogue
-    const float2 *evf;        // mixed epilogue: eps_v as float-float (hi, lo), zero padded to 8 nb
+    const void *t1, *ovov;    // epilogue copies: FP64, float-float pairs (FP64 emulation) or FP32
+    const float2 *evf;        // eps_v as float-float (hi, lo): mixed (zero padded to 8 nb) and FP64 emulation
     const int *tasks;         // [ntask][3]
     const int *orbits;        // [norb][3]
     double *task_e;           // [ntask][2]
@@ -157,6 +157,10 @@ cudaError_t launch_transpose_pad(int kind, const double *in, void *out_hi, void 
 // as float-float pairs [vp]
 cudaError_t launch_epilogue_f32_inputs(const double *t1, const double *ovov, const double *eps_v, float *t1f,
                                        float *ovf, float2 *evf, int o, int v, int vp, cudaStream_t st);
+// FP64-emulation epilogue inputs: t1 [o][v] and ovov [o][v][o][v] converted in
+// place to float-float (hi, lo) pairs; evf[x] = eps_v[x] as a pair, x < v
+cudaError_t launch_epilogue_ff_inputs(double *t1, double *ovov, const double *eps_v, float2 *evf, int o, int v,
+                                      cudaStream_t st);
 // tasks[n] = (i, j, k): the sorted occupied triples i <= j <= k of o orbitals
 // in lexicographic order; orbits[n] = (A, B, C): the sorted block triples
 // A <= B <= C of nb virtual blocks, lexicographic
