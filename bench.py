@@ -42,12 +42,14 @@ FP64_PROBE_TFLOPS = 1.20     # DFMA throughput probe on this machine's GB300
 # reads of one ncu capture at o=16, v=256 (0.807 GB per task) scaled by v^3,
 # plus the U writes (3 v^2 vc x 8 B); valid for this kernel version only
 F64_GEMM_TRAFFIC_BYTES = {(50, 450): int(0.807e9 * (450 / 256) ** 3) + 3 * 450 * 450 * 464 * 8}
-# the same for the tensor-core contractions (SM-pair kernel, FP64 emulation): reads
-# per task of one ncu capture at o=16, v=256 scaled by v^3, plus the U writes
+# the same for the tensor-core contractions (SM-pair kernel, FP64 emulation): DRAM
+# reads plus writes per task of one ncu capture at o=16, v=256, scaled by v^3
+# (the split-precision U is written as 8^3 cubes of the valid values, the
+# emulation's U as [a][b][c] rows of vc)
 TC_GEMM_TRAFFIC_BYTES = {
-    ("bf16x3", 50, 450): int(0.2575e9 * (450 / 256) ** 3) + 3 * 450 * 450 * 464 * 4,
-    ("tf32x3", 50, 450): int(0.539e9 * (450 / 256) ** 3) + 3 * 450 * 450 * 464 * 4,
-    ("fp64_oz", 50, 450): int(0.503e9 * (450 / 256) ** 3) + 3 * 450 * 450 * 464 * 8,
+    ("bf16x3", 50, 450): int((0.2739e9 + 0.1994e9) * (450 / 256) ** 3),
+    ("tf32x3", 50, 450): int((0.5524e9 + 0.2031e9) * (450 / 256) ** 3),
+    ("fp64_oz", 50, 450): int(0.504e9 * (450 / 256) ** 3) + 3 * 450 * 450 * 464 * 8,
 }
 # batched workload: n molecules, o ~ U{4..16}, v ~ U{20..120}, naux = 3(o+v),
 # per-molecule seeds seed+index; FP64 is timed on the first fp64_n of them
