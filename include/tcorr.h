@@ -81,7 +81,8 @@ typedef struct {
     int host_inputs;    /* 0: the array arguments of tcorr_create are device pointers;
                            1: they are host pointers (pageable or pinned), copied in */
     int batch_tasks;    /* tasks per internal batch (batch handle: at most this many tasks per
-                           wave), 0 = chosen from the scratch budget */
+                           wave), 0 = chosen from the scratch budget (single handle: U scratch
+                           of min(16 GiB, free device memory / 8)) */
     int profile;        /* 1: time every kernel class with CUDA events (tcorr_kernel_times) */
     int test_stall;     /* testing only, 0 in normal use: 1 makes the tensor-core kernel withhold
                            one chunk's loads so that a bounded device-side wait expires; the

@@ -130,7 +130,10 @@ tcorr_status tcorr_create(tcorr_t *out, int o, int v, const double *eps_occ,
         if (op.batch_tasks > 0) {
             hs->batch = op.batch_tasks;
         } else {
-            size_t budget = std::min<size_t>((size_t)4 << 30, free_b / 8);
+            // U scratch of up to 16 GiB (an eighth of the free memory at most):
+            // fewer waves per call, each of which drains the kernels and ends
+            // with a task reduction on as many SMs as it has tasks
+            size_t budget = std::min<size_t>((size_t)16 << 30, free_b / 8);
             int64_t b = (int64_t)(budget / u_task_bytes);
             hs->batch = (int)std::max<int64_t>(1, std::min<int64_t>(b, std::min<int64_t>(ntask, 4096)));
         }
