@@ -369,18 +369,18 @@ __global__ void __launch_bounds__(NT, 3) epilogue_kernel(const Wave wv) {
 // W's own index order, in swizzled 8^3 cubes (tcorr_internal.cuh), so the
 // three cubes that make up one W cube sit at the same cube coordinates and
 // W = C0 + C1 + C2 element by element, and the three terms of a cube are
-// stored side by side.  Per orbit two producer warps issue bulk copies
-// (cp.async.bulk) into a free stage, all completing on the stage's mbarrier:
-// one 6 KB copy per distinct slot (6 for three distinct blocks), the 27 8x8
-// ovov sub-blocks (256 B each, from the blocked FP32 copy), the 9 t1 rows
-// and the 3 blocks of float-float virtual energies, the lanes of a warp side
-// by side.  The copy issue rate per warp bounds the pipeline: one producer
-// warp with 2 KB cubes (57 copies per orbit) measured 0.38 ms per task at
-// o=50, v=450, two warps 0.31 ms.  (The small operands as 16-byte cp.async
-// over the lanes measured 17% slower than bulk copies.)  Eight compute warps
-// evaluate the orbit held in the other stage meanwhile.  The
-// cube swizzle makes every W read conflict-free, and the index arithmetic
-// per element orbit is a handful of precomputed offsets.
+// stored side by side.  Per orbit two producer warps fill a free stage, every
+// copy completing on the stage's mbarrier: one 6 KB bulk copy (cp.async.bulk)
+// per distinct slot (6 for three distinct blocks), and 4-row TMA gathers
+// (tile::gather4) from row maps of the blocked FP32 ovov copy (27 8x8
+// sub-blocks: 7 gathers), of t1 (9 rows: 3) and of the float-float virtual
+// energies (3 blocks: 1) -- 17 copies per orbit, issued by the lanes side by
+// side.  The copy issue rate per warp bounded the first versions of this
+// kernel: one warp issuing 57 copies per orbit took 0.38 ms per task at
+// o=50, v=450 (0.27 ms now; 16-byte cp.async for the small operands was
+// slower still).  Eight compute warps evaluate the orbit held in the other
+// stage meanwhile.  The cube swizzle makes every W read conflict-free, and
+// the index arithmetic per element orbit is a handful of precomputed offsets.
 //
 // The per-orbit sum over the CTA goes through shared memory in a fixed
 // order, summed by one compute warp per orbit in rotation, with
@@ -405,7 +405,7 @@ constexpr int EPI_CW = NT / 32;                 // compute warps
 #ifndef EPI_F32_PRODUCERS
 #define EPI_F32_PRODUCERS 2
 #endif
-constexpr int EPI_PRODUCERS = EPI_F32_PRODUCERS;  // producer warps: the U cubes; the small operands
+constexpr int EPI_PRODUCERS = EPI_F32_PRODUCERS;  // producer warps (one warp issues all copies if 1)
 static_assert(EPI_PRODUCERS == 1 || EPI_PRODUCERS == 2, "one or two producer warps");
 constexpr int EPI_THREADS = NT + 32 * EPI_PRODUCERS;
 #ifndef EPI_F32_STAGES
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(EPI_THREADS, EPI_CTAS) epilogue_f32_kernel(con
     __syncthreads();  // the last CTA-wide barrier: from here on the roles meet only at mbarriers
 
     if (warp >= EPI_CW) {
-        const int pw = warp - EPI_CW;  // 0: meta and U cubes; last: the small operands
+        const int pw = warp - EPI_CW;  // 0: meta, U cubes, energies; 1: ovov and t1 gathers
         // ---------------- producer warp ----------------
         // Every lane runs the same decode (uniform loads).  The segment's and
         // the task's fields live in registers and are reloaded only when they
@@ -598,9 +598,9 @@ __global__ void __launch_bounds__(EPI_THREADS, EPI_CTAS) epilogue_f32_kernel(con
             // of their row maps (7, 3 and 1 gathers; a gather's spare rows repeat
             // a valid one and land in the pad rows).  Warp 0 takes the cubes and
             // the energies (and writes the stage's meta), warp 1 ovov and t1.
-            constexpr uint32_t ov_bytes = 7 * 4 * 256 + 3 * 4 * 32, ev_bytes = 4 * 64;
+            constexpr uint32_t ovt1_bytes = 7 * 4 * 256 + 3 * 4 * 32, ev_bytes = 4 * 64;  // gathers write whole 4-row groups
             const uint32_t u_bytes = (uint32_t)nload * 3 * 2048;
-            if (lane == 0 && pw != 0) mbar_expect_tx(full, ov_bytes);
+            if (lane == 0 && pw != 0) mbar_expect_tx(full, ovt1_bytes);
             if (lane == 0 && pw == 0) {
                 EpiMeta &m = meta[stage];
                 m.out = out;
@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(EPI_THREADS, EPI_CTAS) epilogue_f32_kernel(con
                 for (int s = 0; s < 6; s++) m.smap[s] = smap[s];
                 m.kind = (ob0 < ob1 && ob1 < ob2) ? 1 : 2;
                 m.v = v;
-                mbar_expect_tx(full, u_bytes + ev_bytes + (EPI_PRODUCERS == 1 ? ov_bytes : 0u));
+                mbar_expect_tx(full, u_bytes + ev_bytes + (EPI_PRODUCERS == 1 ? ovt1_bytes : 0u));
             }
             __syncwarp();
             const float *Ut = Useg + (int64_t)tb * 3 * ug;
